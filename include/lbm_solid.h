@@ -1,0 +1,174 @@
+/*
+ * lbm_solid.h -- C ABI of the B300 (sm_103a) solid lattice Boltzmann library:
+ * primal LBM sweep, discrete adjoint (ALBM) sweep and gradient for the inverse
+ * problems of arXiv 2609.31347 (linear-elastic solids, D2Q8 moment-space MRT).
+ *
+ * Method references (sections / equations of the paper):
+ *   primal collide + stream ......... Section 3.1, Eqs. local_collide, local_stream,
+ *                                     moments_c, moments_eq, forcing, Table A.1
+ *   objective ....................... Section 3.2, Eqs. node_J, discrete_J
+ *   adjoint fixed point ............. Section 3.3.2, Eqs. adjoint_streaming,
+ *                                     adjoint_collision, adjoint_iteration, Algorithm 1
+ *   gradient ........................ Eq. optimality, Table 1 control maps,
+ *                                     Eq. zero_mean_projection
+ *   convergence monitor ............. Eqs. convergence, convergence_crit
+ *
+ * Conventions
+ *   - Lattice: nx * ny nodes, node n = y*nx + x.  Periodic grids wrap in both
+ *     directions; bounded grids (elliptic plate) mark active nodes and give a
+ *     boundary rule for every link whose source node is not active.
+ *   - Populations are SoA: population k of node n at [k*N + n], k in the D2Q8 order
+ *     Q = ((1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)), N = nx*ny.
+ *     Two-component fields (force, displacement, gradient) are SoA [i*N + n].
+ *   - All arithmetic is IEEE binary64; lattice units with dt = dx^2 (Section 3.1),
+ *     lattice force g = dx^2 F.
+ *   - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA tensors) on
+ *     the handle's device; *_host are host pointers; desc arrays are host arrays.
+ *     All caller pointers are borrowed for the duration of the call only.
+ *   - Calls are stream-ordered on the stream given to lbm_solid_create.  Calls that
+ *     return host scalars (objective, solves that test convergence, gradients of
+ *     scalar controls written to host) synchronise that stream.
+ *   - Errors are return codes; the library never aborts or exits.  After
+ *     LBM_ERR_CUDA the handle is unusable except for lbm_solid_destroy.
+ *     lbm_solid_last_error gives a one-line description of the last failure.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef LBM_SOLID_H
+#define LBM_SOLID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_solid lbm_solid; /* opaque; owns all device state of one lattice */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,           /* invalid argument, size or inconsistent description */
+  LBM_ERR_CUDA = 2,          /* CUDA runtime error (handle unusable afterwards)   */
+  LBM_ERR_OOM = 3,           /* device allocation failed                         */
+  LBM_ERR_STATE = 4,         /* call out of order (e.g. adjoint before primal)    */
+  LBM_ERR_NOT_CONVERGED = 5, /* max_steps reached before the stopping rule held   */
+  LBM_ERR_DIVERGED = 6       /* NaN/Inf detected in the monitored quantity        */
+} lbm_status;
+
+/* Control maps (Table 1 of the paper plus the scalar/field modulus variants). */
+typedef enum {
+  LBM_CTRL_FORCE_FIELD = 0,  /* alpha = nodal force F_n, 2N values (benchmark 2)       */
+  LBM_CTRL_FORCE_BASIS2 = 1, /* F = alpha_1 Phi_1 + alpha_2 Phi_2, 2 values; alpha o F*
+                                (benchmark 1) is Phi_1 = (F*_1,0), Phi_2 = (0,F*_2)    */
+  LBM_CTRL_YOUNG_SCALAR = 2, /* E = alpha^2, 1 value (benchmark 3, Eq. E_substitution) */
+  LBM_CTRL_YOUNG_FIELD = 3   /* E_n = alpha_n^2 per node, N values                     */
+} lbm_control_kind;
+
+/* Link rule codes for bounded grids (per node and direction, host array). */
+enum { LBM_LINK_REGULAR = 0, LBM_LINK_DIRICHLET = 1, LBM_LINK_NEUMANN = 2 };
+
+/* Arithmetic of the sweep kernels. */
+enum {
+  LBM_KERNEL_AUTO = 0, /* fastest variant that matches the FP64 reference       */
+  LBM_KERNEL_FP64 = 1  /* every operation on the FP64 pipe (strict binary64)     */
+};
+
+typedef struct {
+  int nx, ny;               /* nodes per direction, >= 3 each                            */
+  double dx;                /* grid spacing (periodic unit square: 1/nx)                 */
+  int periodic;             /* 1 periodic (Section 4.2), 0 bounded (Section 4.3)         */
+  double E, nu;             /* Young's modulus (> 0) and Poisson ratio (-1 < nu < 1);
+                               YOUNG_* controls override E                              */
+  const uint8_t *node_mask; /* host, N: 1 active, 0 outside; NULL = all active.
+                               Must be NULL (or all 1) for periodic grids               */
+  const uint8_t *link_bc;   /* host, 8N SoA [k*N+n]: LBM_LINK_* for each active node and
+                               incoming direction k; non-regular exactly where the
+                               source node n - c_k is outside.  NULL for periodic grids  */
+  const double *wall_d;     /* host, 2N: Dirichlet displacement at nodes with Dirichlet
+                               links (Eq. disp_Dirichlet), or NULL if none               */
+  const double *wall_T;     /* host, 2N: traction T at nodes with Neumann links
+                               (Eq. disp_Neumann), or NULL if none                       */
+  const double *wall_n;     /* host, 2N: outward unit normal at Neumann nodes, or NULL   */
+  const double *obs_mask;   /* host, N: weight of Omega^J (1/0); NULL = all active nodes  */
+  int control;              /* lbm_control_kind                                          */
+  const double *force;      /* host, 2N: fixed physical body force for YOUNG_* controls
+                               (NULL = zero); ignored for force controls                 */
+  const double *force_basis;/* host, 4N: (Phi_1 [2N], Phi_2 [2N]) for FORCE_BASIS2       */
+  int kernel;               /* LBM_KERNEL_*                                              */
+} lbm_solid_desc;
+
+typedef struct {
+  long max_steps;   /* cap on collide+stream sweeps (>= 1)                               */
+  double tol;       /* tolerance of the stopping rule                                    */
+  int criterion;    /* 0: coefficient of variation of c(t) over a trailing window
+                          (Eq. convergence_crit);
+                       1: residual max|f_C(t)-f_C(t-1)| / max|f_C(t)| < tol             */
+  long window;      /* criterion 0: number of samples in the window (>= 2)              */
+  long check_every; /* sweeps between monitor samples (>= 1)                            */
+  int fixed_steps;  /* nonzero: run exactly max_steps sweeps, no stopping test           */
+} lbm_solve_opts;
+
+typedef struct {
+  long steps;         /* sweeps performed                                              */
+  double last_metric; /* last CV (criterion 0) or residual (criterion 1); 0 if fixed   */
+  double seconds;     /* host wall time of the call                                     */
+} lbm_solve_info;
+
+/* Create a handle for one lattice: validates desc, uploads the geometry, allocates
+   ping-pong population buffers (primal and adjoint), and sets f_S(0) = 0 and a zero
+   control.  stream: cudaStream_t (NULL = legacy default stream). */
+lbm_status lbm_solid_create(const lbm_solid_desc *desc, void *stream, lbm_solid **out);
+lbm_status lbm_solid_destroy(lbm_solid *h);
+
+/* Control alpha on the device: n = 2N (FORCE_FIELD), 2 (FORCE_BASIS2), 1
+   (YOUNG_SCALAR) or N (YOUNG_FIELD).  For YOUNG_* the modulus is alpha^2 (must be
+   > 0).  Resets the primal state to f_S = 0 (Section 4.2.1: zero initial state at
+   every optimisation step) unless keep_state is nonzero (warm start). */
+lbm_status lbm_solid_set_control(lbm_solid *h, const double *alpha_dev, size_t n,
+                                 int keep_state);
+
+/* Target displacement d* on the device (2N); computes Cbar of Eq. node_J. */
+lbm_status lbm_solid_set_target(lbm_solid *h, const double *dstar_dev);
+
+/* Primal solve (Algorithm 2, line 3): sweeps from the current f_S until opts'
+   rule holds.  Returns LBM_ERR_NOT_CONVERGED / LBM_ERR_DIVERGED accordingly (the
+   state is kept either way).  info may be NULL. */
+lbm_status lbm_solid_primal_solve(lbm_solid *h, const lbm_solve_opts *opts,
+                                  lbm_solve_info *info);
+
+/* Objective J of Eq. discrete_J at the current primal state (needs a target). */
+lbm_status lbm_solid_objective(lbm_solid *h, double *J_host);
+
+/* Adjoint solve (Algorithm 1): phi_C(0) = 0, iterate Eq. adjoint_iteration at the
+   current primal state.  Needs set_target and a primal solve after the last
+   set_control. */
+lbm_status lbm_solid_adjoint_solve(lbm_solid *h, const lbm_solve_opts *opts,
+                                   lbm_solve_info *info);
+
+/* Gradient dJ/dalpha (Eq. optimality) from the current primal and adjoint states,
+   written to grad_dev (device, n values as in set_control).  project_zero_mean
+   subtracts the per-component mean over active nodes (Eq. zero_mean_projection;
+   FORCE_FIELD only). */
+lbm_status lbm_solid_gradient(lbm_solid *h, double *grad_dev, size_t n,
+                              int project_zero_mean);
+
+/* Populations: which = 0 primal f_S, 1 adjoint phi_S, 2 adjoint phi_C; 8N device
+   doubles.  set_populations(0) sets f_S (warm start / checkpoint restore);
+   set_populations(2) sets phi_C (adjoint warm start, used by the next adjoint solve
+   when opts.fixed_steps is set and keep is requested via adjoint warm start). */
+lbm_status lbm_solid_get_populations(lbm_solid *h, int which, double *dst_dev);
+lbm_status lbm_solid_set_populations(lbm_solid *h, int which, const double *src_dev);
+
+/* Displacement d = (m10 + g_x/2, m01 + g_y/2) of the primal state (2N device). */
+lbm_status lbm_solid_displacement(lbm_solid *h, double *d_dev);
+
+/* Number of kernel launches this handle has issued (for launch accounting). */
+long lbm_solid_launch_count(const lbm_solid *h);
+
+const char *lbm_status_string(lbm_status s);
+const char *lbm_solid_last_error(const lbm_solid *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_SOLID_H */

@@ -1,0 +1,463 @@
+// Sweep, objective, gradient and reduction kernels of the solid LBM (sm_103a, FP64).
+//
+// Memory layout in HBM: SoA planes of N = nx*ny doubles, population k of node
+// n = y*nx + x at [k*N + n] (x fastest), so a warp's 32 consecutive x of one plane
+// are one coalesced 256-byte access; the pull of Eq. (local_stream) only shifts that
+// window by one element in x and one row in y.
+//
+// Bounded grids add a uint8 node type (0 outside, 1 interior, 2 boundary) and, for
+// boundary nodes only, a compact record: the incoming population of a missing link k
+// is the affine map  f_S,k = sum_j Q_kj f_C,j(x) + s_k  of the node's own
+// post-collision populations (bounce-back for Dirichlet, anti-bounce-back with the
+// wall stress for Neumann), and a bit mask of the regular links.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Pull sources of direction k: x - c_k.
+__constant__ int kCX[8] = {1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kCY[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+
+struct Grid {
+  int nx, ny;
+  long N;  // nodes (plane stride)
+};
+
+struct Bounded {
+  const uint8_t *type;    // N
+  const int *bidx;        // N: boundary record index (valid where type == 2)
+  const double *Q;        // nb * 64, row-major Q[k*8+j]
+  const double *s;        // nb * 8
+  const uint8_t *regmask; // nb: bit k set <=> link k (incoming) is regular
+};
+
+// Neighbour index with periodic wrap.
+__device__ __forceinline__ long wrap_idx(int x, int y, int dx_, int dy_, const Grid &g) {
+  int xs = x + dx_, ys = y + dy_;
+  xs = xs < 0 ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
+  ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+  return (long)ys * g.nx + xs;
+}
+
+// Post-streaming populations at (x, y): f_S,k(x) = f_C,k(x - c_k) (Eq. local_stream),
+// with the boundary rules at boundary nodes.  Returns false for outside nodes.
+template <bool BOUNDED>
+__device__ __forceinline__ bool pull_primal(const double *__restrict__ fin, int x, int y,
+                                            const Grid &g, const Bounded &b, double (&f)[8],
+                                            double &gam_sel) {
+  const long n = (long)y * g.nx + x;
+  gam_sel = 0.0;
+  if (!BOUNDED) {
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const long rm = (long)(y == 0 ? g.ny - 1 : y - 1) * g.nx;
+    const long rp = (long)(y == g.ny - 1 ? 0 : y + 1) * g.nx;
+    const long r0 = (long)y * g.nx;
+    f[0] = __ldg(fin + 0 * g.N + r0 + xm);
+    f[1] = __ldg(fin + 1 * g.N + rm + x);
+    f[2] = __ldg(fin + 2 * g.N + r0 + xp);
+    f[3] = __ldg(fin + 3 * g.N + rp + x);
+    f[4] = __ldg(fin + 4 * g.N + rm + xm);
+    f[5] = __ldg(fin + 5 * g.N + rm + xp);
+    f[6] = __ldg(fin + 6 * g.N + rp + xp);
+    f[7] = __ldg(fin + 7 * g.N + rp + xm);
+    return true;
+  } else {
+    const uint8_t t = b.type[n];
+    if (t == 0) return false;
+    if (t == 1) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+      return true;
+    }
+    const int bi = b.bidx[n];
+    const unsigned reg = b.regmask[bi];
+    double own[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) own[j] = __ldg(fin + j * g.N + n);
+    const double *Q = b.Q + (long)bi * 64;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (reg & (1u << k)) {
+        f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+      } else {
+        double acc = b.s[(long)bi * 8 + k];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc += Q[k * 8 + j] * own[j];
+        f[k] = acc;
+      }
+    }
+    gam_sel = 1.0;
+    return true;
+  }
+}
+
+// Adjoint streaming phi_S = S'^T phi_C at (x, y): phi_S,j(x) = phi_C,j(x + c_j) where
+// that node pulls from x, plus Q^T phi_C(x) at boundary nodes.
+template <bool BOUNDED>
+__device__ __forceinline__ bool pull_adjoint(const double *__restrict__ pin, int x, int y,
+                                             const Grid &g, const Bounded &b, double (&p)[8],
+                                             double &gam_sel) {
+  const long n = (long)y * g.nx + x;
+  gam_sel = 0.0;
+  if (!BOUNDED) {
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const long rm = (long)(y == 0 ? g.ny - 1 : y - 1) * g.nx;
+    const long rp = (long)(y == g.ny - 1 ? 0 : y + 1) * g.nx;
+    const long r0 = (long)y * g.nx;
+    p[0] = __ldg(pin + 0 * g.N + r0 + xp);
+    p[1] = __ldg(pin + 1 * g.N + rp + x);
+    p[2] = __ldg(pin + 2 * g.N + r0 + xm);
+    p[3] = __ldg(pin + 3 * g.N + rm + x);
+    p[4] = __ldg(pin + 4 * g.N + rp + xp);
+    p[5] = __ldg(pin + 5 * g.N + rp + xm);
+    p[6] = __ldg(pin + 6 * g.N + rm + xm);
+    p[7] = __ldg(pin + 7 * g.N + rm + xp);
+    return true;
+  } else {
+    const uint8_t t = b.type[n];
+    if (t == 0) return false;
+    if (t == 1) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        p[k] = __ldg(pin + k * g.N + n + kCX[k] + (long)kCY[k] * g.nx);
+      return true;
+    }
+    const int bi = b.bidx[n];
+    const unsigned reg = b.regmask[bi];
+    double own[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) own[k] = __ldg(pin + k * g.N + n);
+    const double *Q = b.Q + (long)bi * 64;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      // downstream node x + c_j pulls f_C,j(x) iff its link j is regular, i.e. iff the
+      // opposite link jbar at x is regular (its source x - c_jbar = x + c_j is active)
+      const int jb = (j < 4) ? ((j + 2) & 3) : (((j - 4 + 2) & 3) + 4);
+      double acc = (reg & (1u << jb)) ? __ldg(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx)
+                                      : 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc += Q[k * 8 + j] * own[k];  // rows of regular links are 0
+      p[j] = acc;
+    }
+    gam_sel = 1.0;
+    return true;
+  }
+}
+
+// One primal sweep: f_C(t) = C[S' f_C(t-1), g]; optional monitor partial sum of |d|^2.
+template <bool BOUNDED, bool MONITOR>
+__global__ void __launch_bounds__(256) k_primal(const double *__restrict__ fin,
+                                                double *__restrict__ fout,
+                                                const double *__restrict__ g2, Grid g,
+                                                Bounded b, Coef c, double *__restrict__ partial) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  double mon[1] = {0.0};
+  if (x < g.nx && y < g.ny) {
+    const long n = (long)y * g.nx + x;
+    double f[8], gsel;
+    if (pull_primal<BOUNDED>(fin, x, y, g, b, f, gsel)) {
+      double o[8], dxn, dyn;
+      const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+      if (BOUNDED && gsel != 0.0)
+        collide<true>(f, qx, qy, c, o, dxn, dyn);
+      else
+        collide<false>(f, qx, qy, c, o, dxn, dyn);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
+      if (MONITOR) mon[0] = dxn * dxn + dyn * dyn;
+    }
+  }
+  if (MONITOR) {
+    __shared__ double sm[32];
+    block_sum<1>(mon, sm);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = mon[0];
+  }
+}
+
+// Collision only (first sweep from an explicit f_S state): fout = C[fin, g].
+template <bool BOUNDED>
+__global__ void __launch_bounds__(256) k_collide_only(const double *__restrict__ fin,
+                                                      double *__restrict__ fout,
+                                                      const double *__restrict__ g2, Grid g,
+                                                      Bounded b, Coef c) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long n = (long)y * g.nx + x;
+  double gsel = 0.0;
+  if (BOUNDED) {
+    const uint8_t t = b.type[n];
+    if (t == 0) return;
+    gsel = t == 2 ? 1.0 : 0.0;
+  }
+  double f[8], o[8], dxn, dyn;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f[k] = fin[k * g.N + n];
+  if (gsel != 0.0)
+    collide<true>(f, g2[n], g2[g.N + n], c, o, dxn, dyn);
+  else
+    collide<false>(f, g2[n], g2[g.N + n], c, o, dxn, dyn);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
+}
+
+// f_S = S' f_C (no collision): checkpoint read-out of the primal state.
+template <bool BOUNDED>
+__global__ void k_pull_primal(const double *__restrict__ fin, double *__restrict__ fs, Grid g,
+                              Bounded b) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long n = (long)y * g.nx + x;
+  double f[8], gsel;
+  if (!pull_primal<BOUNDED>(fin, x, y, g, b, f, gsel))
+    for (int k = 0; k < 8; ++k) f[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) fs[k * g.N + n] = f[k];
+}
+
+// phi_S = S'^T phi_C (no collision).
+template <bool BOUNDED>
+__global__ void k_pull_adjoint(const double *__restrict__ pin, double *__restrict__ ps, Grid g,
+                               Bounded b) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long n = (long)y * g.nx + x;
+  double p[8], gsel;
+  if (!pull_adjoint<BOUNDED>(pin, x, y, g, b, p, gsel))
+    for (int k = 0; k < 8; ++k) p[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) ps[k * g.N + n] = p[k];
+}
+
+// Displacement of the primal state (source = explicit f_S or f_C(t-1) via pull).
+template <bool BOUNDED, bool FROM_FC>
+__global__ void k_displacement(const double *__restrict__ src, const double *__restrict__ g2,
+                               double *__restrict__ d, Grid g, Bounded b) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long n = (long)y * g.nx + x;
+  double f[8], gsel;
+  bool act;
+  if (FROM_FC) {
+    act = pull_primal<BOUNDED>(src, x, y, g, b, f, gsel);
+  } else {
+    act = !BOUNDED || b.type[n] != 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = src[k * g.N + n];
+  }
+  double dxn = 0.0, dyn = 0.0;
+  if (act) {
+    dxn = (f[0] - f[2]) + (f[4] - f[6]) - (f[5] - f[7]) + 2.0 * g2[n];
+    dyn = (f[1] - f[3]) + (f[4] - f[6]) + (f[5] - f[7]) + 2.0 * g2[g.N + n];
+  }
+  d[n] = dxn;
+  d[g.N + n] = dyn;
+}
+
+// Objective partials and adjoint source: e = d - d*, J_n = 0.5 obs |e|^2 (times
+// dx^2 / Cbar outside), r = (dx^2 / Cbar) obs e  (Eqs. node_J, discrete_J;
+// (dJ/df_S)_k = r . c_k).
+template <bool BOUNDED, bool FROM_FC>
+__global__ void __launch_bounds__(256) k_objective(const double *__restrict__ src,
+                                                   const double *__restrict__ g2,
+                                                   const double *__restrict__ dstar,
+                                                   const double *__restrict__ obs,
+                                                   double *__restrict__ r, double scale, Grid g,
+                                                   Bounded b, double *__restrict__ partial) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  double acc[1] = {0.0};
+  if (x < g.nx && y < g.ny) {
+    const long n = (long)y * g.nx + x;
+    double f[8], gsel;
+    bool act;
+    if (FROM_FC) {
+      act = pull_primal<BOUNDED>(src, x, y, g, b, f, gsel);
+    } else {
+      act = !BOUNDED || b.type[n] != 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = src[k * g.N + n];
+    }
+    double rx = 0.0, ry = 0.0;
+    if (act) {
+      const double w = obs ? obs[n] : 1.0;
+      const double ex = (f[0] - f[2]) + (f[4] - f[6]) - (f[5] - f[7]) + 2.0 * g2[n] - dstar[n];
+      const double ey = (f[1] - f[3]) + (f[4] - f[6]) + (f[5] - f[7]) + 2.0 * g2[g.N + n] -
+                        dstar[g.N + n];
+      acc[0] = w * (ex * ex + ey * ey);
+      rx = scale * w * ex;
+      ry = scale * w * ey;
+    }
+    r[n] = rx;
+    r[g.N + n] = ry;
+  }
+  __shared__ double sm[32];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
+}
+
+// One adjoint sweep: phi_C(k+1) = A^T S'^T phi_C(k) - j; optional monitor of |d^phi|^2.
+template <bool BOUNDED, bool MONITOR>
+__global__ void __launch_bounds__(256) k_adjoint(const double *__restrict__ pin,
+                                                 double *__restrict__ pout,
+                                                 const double *__restrict__ r, Grid g,
+                                                 Bounded b, Coef c, double *__restrict__ partial) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  double mon[1] = {0.0};
+  if (x < g.nx && y < g.ny) {
+    const long n = (long)y * g.nx + x;
+    double p[8], gsel;
+    if (pull_adjoint<BOUNDED>(pin, x, y, g, b, p, gsel)) {
+      double o[8], ax, ay;
+      if (BOUNDED && gsel != 0.0)
+        collide_T<true>(p, __ldg(r + n), __ldg(r + g.N + n), c, o, ax, ay);
+      else
+        collide_T<false>(p, __ldg(r + n), __ldg(r + g.N + n), c, o, ax, ay);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
+      if (MONITOR) mon[0] = ax * ax + ay * ay;
+    }
+  }
+  if (MONITOR) {
+    __shared__ double sm[32];
+    block_sum<1>(mon, sm);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = mon[0];
+  }
+}
+
+// Force gradient (Eq. optimality): dJ/dF_n = dx^2 (r_n / 2 - (dC/dg)^T phi_S,n).
+// MODE 0: write the 2N field (and its component sums for the zero-mean projection);
+// MODE 1: reduce against the two basis fields: dJ/dalpha_i = sum_n Phi_i . dJ/dF_n.
+template <bool BOUNDED, int MODE>
+__global__ void __launch_bounds__(256) k_grad_force(const double *__restrict__ pin,
+                                                    const double *__restrict__ r,
+                                                    const double *__restrict__ basis,
+                                                    double *__restrict__ grad, double dx2, Grid g,
+                                                    Bounded b, double *__restrict__ partial) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  double acc[2] = {0.0, 0.0};
+  if (x < g.nx && y < g.ny) {
+    const long n = (long)y * g.nx + x;
+    double p[8], gsel;
+    double gx = 0.0, gy = 0.0;
+    if (pull_adjoint<BOUNDED>(pin, x, y, g, b, p, gsel)) {
+      double sx, sy;
+      force_sensitivity(p, sx, sy);
+      gx = dx2 * (0.5 * r[n] - sx);
+      gy = dx2 * (0.5 * r[g.N + n] - sy);
+    }
+    if (MODE == 0) {
+      grad[n] = gx;
+      grad[g.N + n] = gy;
+      acc[0] = gx;
+      acc[1] = gy;
+    } else {
+      acc[0] = basis[n] * gx + basis[g.N + n] * gy;
+      acc[1] = basis[2 * g.N + n] * gx + basis[3 * g.N + n] * gy;
+    }
+  }
+  __shared__ double sm[64];
+  block_sum<2>(acc, sm);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const long bl = blockIdx.y * gridDim.x + blockIdx.x;
+    partial[bl * 2 + 0] = acc[0];
+    partial[bl * 2 + 1] = acc[1];
+  }
+}
+
+// Subtract per-component means over active nodes (Eq. zero_mean_projection).
+template <bool BOUNDED>
+__global__ void k_subtract_mean(double *__restrict__ v, const double *__restrict__ mean, Grid g,
+                                Bounded b) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long n = (long)y * g.nx + x;
+  if (BOUNDED && b.type[n] == 0) return;
+  v[n] -= mean[0];
+  v[g.N + n] -= mean[1];
+}
+
+// Residual partials: max |a - b| and max |a| over all planes.
+__global__ void __launch_bounds__(256) k_residual(const double *__restrict__ a,
+                                                  const double *__restrict__ bb, long total,
+                                                  double *__restrict__ partial) {
+  double v[2] = {0.0, 0.0};
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    const double ai = a[i];
+    v[0] = fmax(v[0], fabs(ai - bb[i]));
+    v[1] = fmax(v[1], fabs(ai));
+  }
+  __shared__ double sm[64];
+  block_max<2>(v, sm);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x * 2 + 0] = v[0];
+    partial[blockIdx.x * 2 + 1] = v[1];
+  }
+}
+
+// Second pass: out[v] = reduce over nb partials (fixed order, one block).  op 0 sum, 1 max.
+__global__ void __launch_bounds__(256) k_finish(const double *__restrict__ partial, long nb,
+                                                int nv, int op, double scale,
+                                                double *__restrict__ out) {
+  __shared__ double sm[32 * 4];
+  for (int v = 0; v < nv; ++v) {
+    double acc[1] = {0.0};
+    for (long i = threadIdx.x; i < nb; i += blockDim.x) {
+      const double t = partial[i * nv + v];
+      acc[0] = op == 0 ? acc[0] + t : fmax(acc[0], t);
+    }
+    if (op == 0)
+      block_sum<1>(acc, sm);
+    else
+      block_max<1>(acc, sm);
+    if (threadIdx.x == 0) out[v] = acc[0] * scale;
+    __syncthreads();
+  }
+}
+
+// Quarter lattice force q = g / 4 = dx^2 (a1 Phi_1 + a2 Phi_2) / 4 from the two basis
+// fields, or q = dx^2 F / 4 from a nodal force (alpha == nullptr).
+__global__ void k_set_force(double *__restrict__ g2, const double *__restrict__ src,
+                            const double *__restrict__ basis, const double *__restrict__ alpha2,
+                            double dx2, long N, const uint8_t *__restrict__ type) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 2 * N;
+       i += (long)gridDim.x * blockDim.x) {
+    double v;
+    if (alpha2)
+      v = alpha2[0] * basis[i] + alpha2[1] * basis[2 * N + i];
+    else
+      v = src ? src[i] : 0.0;
+    const long n = i < N ? i : i - N;
+    if (type && type[n] == 0) v = 0.0;
+    g2[i] = dx2 * v;
+  }
+}
+
+// Cbar partial sums: sum_n obs |d*_n|^2 (times dx^2 outside).
+template <bool BOUNDED>
+__global__ void __launch_bounds__(256) k_cbar(const double *__restrict__ dstar,
+                                              const double *__restrict__ obs, Grid g, Bounded b,
+                                              double *__restrict__ partial) {
+  double acc[1] = {0.0};
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < g.N;
+       n += (long)gridDim.x * blockDim.x) {
+    if (BOUNDED && b.type[n] == 0) continue;
+    const double w = obs ? obs[n] : 1.0;
+    acc[0] += w * (dstar[n] * dstar[n] + dstar[g.N + n] * dstar[g.N + n]);
+  }
+  __shared__ double sm[32];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+}
+
+}  // namespace lbm

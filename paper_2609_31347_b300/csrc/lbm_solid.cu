@@ -1,0 +1,702 @@
+// Host side of the C ABI declared in include/lbm_solid.h: handle, validation, the
+// primal / adjoint solve loops with their stopping rules, and kernel launches.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_boundary.cuh"
+#include "lbm_kernels.cuh"
+#include "lbm_solid.h"
+
+using namespace lbm;
+
+struct lbm_solid {
+  int nx = 0, ny = 0;
+  long N = 0;
+  double dx = 0.0;
+  int periodic = 1;
+  double nu = 0.0, E = 0.0;
+  int control = 0, kernel = 0;
+  cudaStream_t stream = nullptr;
+  Grid grid{};
+  Bounded bnd{};
+  Coef coef{};
+  Material mat{};
+  long n_active = 0;
+  bool has_neumann = false;
+  // device buffers
+  double *fA = nullptr, *fB = nullptr, *pA = nullptr, *pB = nullptr;
+  double *g2 = nullptr, *r2 = nullptr, *dstar = nullptr, *obs = nullptr;
+  double *basis = nullptr, *Fbase = nullptr;
+  uint8_t *type = nullptr, *regmask = nullptr;
+  int *bidx = nullptr;
+  double *Q = nullptr, *s = nullptr;
+  BoundaryNode *bnodes = nullptr;
+  long nb = 0;
+  double *partial = nullptr;
+  long partial_cap = 0;
+  double *dres = nullptr;
+  double *hres = nullptr;  // pinned
+  // state
+  double *fcur = nullptr, *fnext = nullptr, *pcur = nullptr, *pnext = nullptr;
+  bool fcur_is_fs = true;  // fcur holds an explicit f_S; otherwise f_C(t-1)
+  bool have_target = false, adjoint_valid = false, adj_warm = false;
+  double cbar = 0.0;
+  long launches = 0;
+  bool broken = false;
+  std::string err;
+  dim3 blk, grd;
+  long nblocks2d = 0;
+};
+
+namespace {
+
+lbm_status fail(lbm_solid *h, lbm_status st, const std::string &msg) {
+  if (h) {
+    h->err = msg;
+    if (st == LBM_ERR_CUDA) h->broken = true;
+  }
+  return st;
+}
+
+#define CK(h, call)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+#define LAUNCHED(h)                                                                     \
+  do {                                                                                  \
+    ++(h)->launches;                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(h, LBM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr double kTh = 1.0 / 3.0;
+
+// Material map (Eqs. lambda, mu, K) and relaxation (Table A.1, Eq. relaxation, Eq. gamma).
+bool material_coefs(double E, double nu, bool bounded, bool neumann, Coef &c, Material &m,
+                    std::string &why) {
+  if (!(E > 0.0) || !std::isfinite(E)) { why = "Young's modulus must be > 0"; return false; }
+  if (!(nu > -1.0 && nu < 1.0)) { why = "Poisson ratio must lie in (-1, 1)"; return false; }
+  const double mu = E / (2.0 * (1.0 + nu));
+  const double K = E / (2.0 * (1.0 - nu));
+  const double t11 = mu / kTh, ts = 2.0 * K / (1.0 + kTh), td = 2.0 * mu / (1.0 - kTh);
+  const double w11 = 1.0 / (t11 + 0.5), ws = 1.0 / (ts + 0.5), wd = 1.0 / (td + 0.5);
+  c.c11 = 1.0 - w11; c.cs = 1.0 - ws; c.cd = 1.0 - wd;
+  c.w11 = w11; c.ws = ws; c.wd = wd; c.K = K;
+  c.gam = 0.0;
+  if (bounded) {
+    if (std::fabs(ts - 0.5) < 1e-14) { why = "tau_s = tau_f = 1/2 makes gamma singular"; return false; }
+    c.gam = kTh * 0.5 / ((1.0 + kTh) * (ts - 0.5));
+    if (neumann && (std::fabs(c.c11) < 1e-12 || std::fabs(c.cs) < 1e-12 || std::fabs(c.cd) < 1e-12)) {
+      why = "a relaxed moment with omega = 1 leaves the Neumann wall stress undefined";
+      return false;
+    }
+  }
+  c.q11 = 0.25 * c.c11; c.qs = 0.25 * c.cs; c.qd = 0.25 * c.cd;
+  c.qs_b = c.cs * (0.25 + 0.5 * c.gam);
+  c.P_b = -0.25 * c.gam * c.cs;
+  m.w11 = w11; m.ws = ws; m.wd = wd; m.K = K;
+  return true;
+}
+
+lbm_status setup_boundary(lbm_solid *h) {
+  if (h->periodic || h->nb == 0) return LBM_OK;
+  const unsigned threads = 128;
+  const unsigned blocks = (unsigned)((h->nb + threads - 1) / threads);
+  k_boundary_setup<<<blocks, threads, 0, h->stream>>>(h->bnodes, h->nb, h->mat, h->dx, h->Q, h->s);
+  LAUNCHED(h);
+  return LBM_OK;
+}
+
+lbm_status set_material(lbm_solid *h, double E) {
+  Coef c{};
+  Material m{};
+  std::string why;
+  if (!material_coefs(E, h->nu, !h->periodic, h->has_neumann, c, m, why))
+    return fail(h, LBM_ERR_ARG, why);
+  c.dx = h->dx;
+  h->coef = c;
+  h->mat = m;
+  h->E = E;
+  return setup_boundary(h);
+}
+
+lbm_status finish(lbm_solid *h, long nb, int nv, int op, double scale, double *out) {
+  k_finish<<<1, 256, 0, h->stream>>>(h->partial, nb, nv, op, scale, out);
+  LAUNCHED(h);
+  return LBM_OK;
+}
+
+lbm_status fetch(lbm_solid *h, int nv) {
+  CK(h, cudaMemcpyAsync(h->hres, h->dres, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+// One primal sweep; optional monitor partials (nblocks2d sums of |d|^2).
+lbm_status primal_sweep(lbm_solid *h, bool monitor) {
+  if (h->fcur_is_fs) {
+    if (h->periodic)
+      k_collide_only<false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef);
+    else
+      k_collide_only<true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef);
+  } else if (h->periodic) {
+    if (monitor)
+      k_primal<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->partial);
+    else
+      k_primal<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, nullptr);
+  } else {
+    if (monitor)
+      k_primal<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->partial);
+    else
+      k_primal<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, nullptr);
+  }
+  LAUNCHED(h);
+  std::swap(h->fcur, h->fnext);
+  h->fcur_is_fs = false;
+  return LBM_OK;
+}
+
+lbm_status adjoint_sweep(lbm_solid *h, bool monitor) {
+  if (h->periodic) {
+    if (monitor)
+      k_adjoint<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->partial);
+    else
+      k_adjoint<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, nullptr);
+  } else {
+    if (monitor)
+      k_adjoint<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->partial);
+    else
+      k_adjoint<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, nullptr);
+  }
+  LAUNCHED(h);
+  std::swap(h->pcur, h->pnext);
+  return LBM_OK;
+}
+
+lbm_status residual(lbm_solid *h, const double *a, const double *b, double &res) {
+  const long total = 8 * h->N;
+  long blocks = (total + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  k_residual<<<(unsigned)blocks, 256, 0, h->stream>>>(a, b, total, h->partial);
+  LAUNCHED(h);
+  lbm_status st = finish(h, blocks, 2, 1, 1.0, h->dres);
+  if (st) return st;
+  if ((st = fetch(h, 2))) return st;
+  res = h->hres[1] > 0.0 ? h->hres[0] / h->hres[1] : (h->hres[0] > 0.0 ? INFINITY : 0.0);
+  if (!std::isfinite(h->hres[0]) || !std::isfinite(h->hres[1])) res = NAN;
+  return LBM_OK;
+}
+
+// Shared stopping loop of the primal and adjoint solves.
+template <class Sweep, class Resid>
+lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *info, Sweep sweep,
+                      Resid resid, bool can_monitor_first) {
+  const auto t0 = std::chrono::steady_clock::now();
+  long steps = 0;
+  double metric = 0.0;
+  lbm_status result = LBM_OK;
+  if (o->fixed_steps) {
+    for (; steps < o->max_steps; ++steps) {
+      lbm_status st = sweep(false);
+      if (st) return st;
+    }
+  } else {
+    std::deque<double> win;
+    bool done = false;
+    while (!done && steps < o->max_steps) {
+      long k = o->check_every;
+      if (k > o->max_steps - steps) k = o->max_steps - steps;
+      for (long i = 0; i < k; ++i) {
+        const bool last = (i == k - 1);
+        lbm_status st = sweep(last && o->criterion == 0);
+        if (st) return st;
+        ++steps;
+      }
+      if (steps < 2 && !can_monitor_first) continue;
+      double v = 0.0;
+      if (o->criterion == 0) {
+        lbm_status st = finish(h, h->nblocks2d, 1, 0, h->n_active ? 1.0 / h->n_active : 0.0, h->dres);
+        if (st) return st;
+        if ((st = fetch(h, 1))) return st;
+        v = h->hres[0];
+        if (!std::isfinite(v)) { metric = v; result = LBM_ERR_DIVERGED; break; }
+        win.push_back(v);
+        if ((long)win.size() > o->window) win.pop_front();
+        if ((long)win.size() == o->window) {
+          double mean = 0.0, var = 0.0;
+          for (double c : win) mean += c;
+          mean /= (double)win.size();
+          for (double c : win) var += (c - mean) * (c - mean);
+          const double sd = std::sqrt(var / (double)win.size());
+          metric = mean > 0.0 ? sd / mean : (sd == 0.0 ? 0.0 : INFINITY);
+          if (metric < o->tol) done = true;
+        }
+      } else {
+        lbm_status st = resid(v);
+        if (st) return st;
+        metric = v;
+        if (std::isnan(v)) { result = LBM_ERR_DIVERGED; break; }
+        if (v < o->tol) done = true;
+      }
+    }
+    if (result == LBM_OK && !done) result = LBM_ERR_NOT_CONVERGED;
+  }
+  if (info) {
+    info->steps = steps;
+    info->last_metric = metric;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (result == LBM_ERR_NOT_CONVERGED) h->err = "max_steps reached before the stopping rule held";
+  if (result == LBM_ERR_DIVERGED) h->err = "non-finite monitor value";
+  return result;
+}
+
+lbm_status check_opts(lbm_solid *h, const lbm_solve_opts *o) {
+  if (!o) return fail(h, LBM_ERR_ARG, "opts is NULL");
+  if (o->max_steps < 1) return fail(h, LBM_ERR_ARG, "max_steps must be >= 1");
+  if (!o->fixed_steps) {
+    if (o->check_every < 1) return fail(h, LBM_ERR_ARG, "check_every must be >= 1");
+    if (o->criterion == 0 && o->window < 2) return fail(h, LBM_ERR_ARG, "window must be >= 2");
+    if (o->criterion != 0 && o->criterion != 1) return fail(h, LBM_ERR_ARG, "criterion must be 0 or 1");
+    if (!(o->tol > 0.0)) return fail(h, LBM_ERR_ARG, "tol must be > 0");
+  }
+  return LBM_OK;
+}
+
+lbm_status objective_partials(lbm_solid *h) {
+  const double scale = h->dx * h->dx / h->cbar;
+  if (h->periodic) {
+    if (h->fcur_is_fs)
+      k_objective<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, h->dstar, h->obs, h->r2, scale, h->grid, h->bnd, h->partial);
+    else
+      k_objective<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, h->dstar, h->obs, h->r2, scale, h->grid, h->bnd, h->partial);
+  } else {
+    if (h->fcur_is_fs)
+      k_objective<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, h->dstar, h->obs, h->r2, scale, h->grid, h->bnd, h->partial);
+    else
+      k_objective<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, h->dstar, h->obs, h->r2, scale, h->grid, h->bnd, h->partial);
+  }
+  LAUNCHED(h);
+  return LBM_OK;
+}
+
+void free_all(lbm_solid *h) {
+  void *bufs[] = {h->fA, h->fB, h->pA, h->pB, h->g2, h->r2, h->dstar, h->obs, h->basis, h->Fbase,
+                  h->type, h->regmask, h->bidx, h->Q, h->s, h->bnodes, h->partial, h->dres};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  if (h->hres) cudaFreeHost(h->hres);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_status_string(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_OOM: return "out of device memory";
+    case LBM_ERR_STATE: return "call out of order";
+    case LBM_ERR_NOT_CONVERGED: return "not converged";
+    case LBM_ERR_DIVERGED: return "diverged";
+  }
+  return "unknown status";
+}
+
+const char *lbm_solid_last_error(const lbm_solid *h) { return h ? h->err.c_str() : "null handle"; }
+
+long lbm_solid_launch_count(const lbm_solid *h) { return h ? h->launches : -1; }
+
+lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **out) {
+  if (!out || !d) return LBM_ERR_ARG;
+  *out = nullptr;
+  if (d->nx < 3 || d->ny < 3) return LBM_ERR_ARG;
+  if ((long)d->nx * d->ny > (1L << 31) / 8) return LBM_ERR_ARG;  // 8N plane offsets fit int64 and index math
+  if (!(d->dx > 0.0) || !std::isfinite(d->dx)) return LBM_ERR_ARG;
+  if (d->control < LBM_CTRL_FORCE_FIELD || d->control > LBM_CTRL_YOUNG_FIELD) return LBM_ERR_ARG;
+  if (d->kernel != LBM_KERNEL_AUTO && d->kernel != LBM_KERNEL_FP64) return LBM_ERR_ARG;
+  if (d->control == LBM_CTRL_FORCE_BASIS2 && !d->force_basis) return LBM_ERR_ARG;
+  if (d->control == LBM_CTRL_YOUNG_FIELD) return LBM_ERR_ARG;  // per-node moduli: not built yet
+  lbm_solid *h = new (std::nothrow) lbm_solid();
+  if (!h) return LBM_ERR_OOM;
+  h->nx = d->nx; h->ny = d->ny; h->N = (long)d->nx * d->ny; h->dx = d->dx;
+  h->periodic = d->periodic ? 1 : 0; h->nu = d->nu; h->control = d->control; h->kernel = d->kernel;
+  h->stream = (cudaStream_t)stream;
+  h->grid = Grid{d->nx, d->ny, h->N};
+  const long N = h->N;
+  auto bail = [&](lbm_status st) { free_all(h); delete h; return st; };
+
+  // ---- geometry (host validation, compact boundary records) -----------------------
+  std::vector<uint8_t> type(N, 1);
+  std::vector<int> bidx(N, -1);
+  std::vector<BoundaryNode> bn;
+  std::vector<uint8_t> regm;
+  if (h->periodic) {
+    if (d->link_bc) return bail(LBM_ERR_ARG);
+    if (d->node_mask)
+      for (long n = 0; n < N; ++n)
+        if (d->node_mask[n] != 1) return bail(LBM_ERR_ARG);
+    h->n_active = N;
+  } else {
+    if (!d->link_bc) return bail(LBM_ERR_ARG);
+    for (long n = 0; n < N; ++n) type[n] = d->node_mask ? (d->node_mask[n] ? 1 : 0) : 1;
+    const int cx[8] = {1, 0, -1, 0, 1, -1, -1, 1}, cy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+    h->n_active = 0;
+    for (long n = 0; n < N; ++n) {
+      if (!type[n]) continue;
+      ++h->n_active;
+      const int x = (int)(n % d->nx), y = (int)(n / d->nx);
+      BoundaryNode b{};
+      uint8_t reg = 0;
+      bool any = false;
+      for (int k = 0; k < 8; ++k) {
+        const int xs = x - cx[k], ys = y - cy[k];
+        const bool src_active = xs >= 0 && xs < d->nx && ys >= 0 && ys < d->ny &&
+                                type[(long)ys * d->nx + xs] != 0;
+        const uint8_t code = d->link_bc[(long)k * N + n];
+        if (code > 2) return bail(LBM_ERR_ARG);
+        if (src_active != (code == 0)) return bail(LBM_ERR_ARG);
+        b.code[k] = code;
+        if (code == 0) reg |= (uint8_t)(1u << k);
+        if (code == 1) {
+          if (!d->wall_d) return bail(LBM_ERR_ARG);
+          b.wd[0] = d->wall_d[n]; b.wd[1] = d->wall_d[N + n];
+        }
+        if (code == 2) {
+          if (!d->wall_T || !d->wall_n) return bail(LBM_ERR_ARG);
+          b.T[0] = d->wall_T[n]; b.T[1] = d->wall_T[N + n];
+          b.nrm[0] = d->wall_n[n]; b.nrm[1] = d->wall_n[N + n];
+          h->has_neumann = true;
+        }
+        any |= code != 0;
+      }
+      if (any) {
+        type[n] = 2;
+        bidx[n] = (int)bn.size();
+        bn.push_back(b);
+        regm.push_back(reg);
+      }
+    }
+    if (h->n_active == 0) return bail(LBM_ERR_ARG);
+  }
+  h->nb = (long)bn.size();
+
+  // ---- device buffers ---------------------------------------------------------------
+  const size_t pop = sizeof(double) * 8 * N, two = sizeof(double) * 2 * N;
+  unsigned bx = 128;
+  while (bx > 32 && bx / 2 >= (unsigned)d->nx) bx /= 2;
+  h->blk = dim3(bx, 256 / bx);
+  h->grd = dim3((d->nx + h->blk.x - 1) / h->blk.x, (d->ny + h->blk.y - 1) / h->blk.y);
+  h->nblocks2d = (long)h->grd.x * h->grd.y;
+  h->partial_cap = 4 * (h->nblocks2d > 148 * 8 ? h->nblocks2d : 148 * 8);
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) \
+  if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
+  ALLOC(h->fA, pop); ALLOC(h->fB, pop); ALLOC(h->pA, pop); ALLOC(h->pB, pop);
+  ALLOC(h->g2, two); ALLOC(h->r2, two); ALLOC(h->dstar, two);
+  ALLOC(h->partial, sizeof(double) * h->partial_cap);
+  ALLOC(h->dres, sizeof(double) * 8);
+  if (d->obs_mask) ALLOC(h->obs, sizeof(double) * N);
+  if (d->control == LBM_CTRL_FORCE_BASIS2) ALLOC(h->basis, 2 * two);
+  if (d->control >= LBM_CTRL_YOUNG_SCALAR) ALLOC(h->Fbase, two);
+  if (!h->periodic) {
+    ALLOC(h->type, N);
+    ALLOC(h->bidx, sizeof(int) * N);
+    if (h->nb) {
+      ALLOC(h->regmask, h->nb);
+      ALLOC(h->bnodes, sizeof(BoundaryNode) * h->nb);
+      ALLOC(h->Q, sizeof(double) * 64 * h->nb);
+      ALLOC(h->s, sizeof(double) * 8 * h->nb);
+    }
+  }
+#undef ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hres, sizeof(double) * 8);
+  if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);
+
+  // ---- uploads (synchronous: desc arrays are pageable host memory) -----------------
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  if (d->obs_mask) {
+    std::vector<double> ob(d->obs_mask, d->obs_mask + N);
+    for (long n = 0; n < N; ++n)
+      if (!type[n]) ob[n] = 0.0;
+    up(h->obs, ob.data(), sizeof(double) * N);
+  }
+  if (h->basis) {
+    std::vector<double> bs(d->force_basis, d->force_basis + 4 * N);
+    up(h->basis, bs.data(), 2 * two);
+  }
+  if (!h->periodic) {
+    up(h->type, type.data(), N);
+    up(h->bidx, bidx.data(), sizeof(int) * N);
+    if (h->nb) {
+      up(h->regmask, regm.data(), h->nb);
+      up(h->bnodes, bn.data(), sizeof(BoundaryNode) * h->nb);
+    }
+    h->bnd = Bounded{h->type, h->bidx, h->Q, h->s, h->regmask};
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->fA, 0, pop, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->fB, 0, pop, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->pA, 0, pop, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->pB, 0, pop, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->g2, 0, two, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->r2, 0, two, h->stream);
+  if (e != cudaSuccess) return bail(LBM_ERR_CUDA);
+  h->fcur = h->fA; h->fnext = h->fB; h->pcur = h->pA; h->pnext = h->pB;
+  h->fcur_is_fs = true;
+
+  // ---- material and fixed force -----------------------------------------------------
+  if (set_material(h, d->E) != LBM_OK) return bail(LBM_ERR_ARG);
+  if (h->Fbase) {
+    if (d->force) {
+      std::vector<double> F(d->force, d->force + 2 * N);
+      for (long n = 0; n < N; ++n)
+        if (!type[n]) F[n] = F[N + n] = 0.0;
+      up(h->Fbase, F.data(), two);
+      if (e != cudaSuccess) return bail(LBM_ERR_CUDA);
+    } else if (cudaMemsetAsync(h->Fbase, 0, two, h->stream) != cudaSuccess) {
+      return bail(LBM_ERR_CUDA);
+    }
+    k_set_force<<<148 * 4, 256, 0, h->stream>>>(h->g2, h->Fbase, nullptr, nullptr, 0.25 * h->dx * h->dx, N,
+                                              h->periodic ? nullptr : h->type);
+    ++h->launches;
+    if (cudaGetLastError() != cudaSuccess) return bail(LBM_ERR_CUDA);
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(LBM_ERR_CUDA);
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_solid_destroy(lbm_solid *h) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return LBM_OK;
+}
+
+lbm_status lbm_solid_set_control(lbm_solid *h, const double *alpha, size_t n, int keep_state) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!alpha) return fail(h, LBM_ERR_ARG, "alpha is NULL");
+  const double dx2 = 0.25 * h->dx * h->dx;  // q = g / 4
+  const uint8_t *tp = h->periodic ? nullptr : h->type;
+  switch (h->control) {
+    case LBM_CTRL_FORCE_FIELD:
+      if (n != (size_t)(2 * h->N)) return fail(h, LBM_ERR_ARG, "FORCE_FIELD control needs 2N values");
+      k_set_force<<<148 * 4, 256, 0, h->stream>>>(h->g2, alpha, nullptr, nullptr, dx2, h->N, tp);
+      LAUNCHED(h);
+      break;
+    case LBM_CTRL_FORCE_BASIS2:
+      if (n != 2) return fail(h, LBM_ERR_ARG, "FORCE_BASIS2 control needs 2 values");
+      k_set_force<<<148 * 4, 256, 0, h->stream>>>(h->g2, nullptr, h->basis, alpha, dx2, h->N, tp);
+      LAUNCHED(h);
+      break;
+    case LBM_CTRL_YOUNG_SCALAR: {
+      if (n != 1) return fail(h, LBM_ERR_ARG, "YOUNG_SCALAR control needs 1 value");
+      CK(h, cudaMemcpyAsync(h->hres, alpha, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(h, cudaStreamSynchronize(h->stream));
+      const lbm_status st = set_material(h, h->hres[0] * h->hres[0]);
+      if (st) return st;
+      break;
+    }
+    default:
+      return fail(h, LBM_ERR_ARG, "unsupported control kind");
+  }
+  if (!keep_state) {
+    CK(h, cudaMemsetAsync(h->fcur, 0, sizeof(double) * 8 * h->N, h->stream));
+    h->fcur_is_fs = true;
+  }
+  h->adjoint_valid = false;
+  h->adj_warm = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_solid_set_target(lbm_solid *h, const double *dstar) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!dstar) return fail(h, LBM_ERR_ARG, "dstar is NULL");
+  CK(h, cudaMemcpyAsync(h->dstar, dstar, sizeof(double) * 2 * h->N, cudaMemcpyDeviceToDevice, h->stream));
+  long blocks = (h->N + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (h->periodic)
+    k_cbar<false><<<(unsigned)blocks, 256, 0, h->stream>>>(h->dstar, h->obs, h->grid, h->bnd, h->partial);
+  else
+    k_cbar<true><<<(unsigned)blocks, 256, 0, h->stream>>>(h->dstar, h->obs, h->grid, h->bnd, h->partial);
+  LAUNCHED(h);
+  lbm_status st = finish(h, blocks, 1, 0, h->dx * h->dx, h->dres);
+  if (st) return st;
+  if ((st = fetch(h, 1))) return st;
+  if (!(h->hres[0] > 0.0) || !std::isfinite(h->hres[0]))
+    return fail(h, LBM_ERR_ARG, "target has zero norm on the observation domain (Cbar = 0)");
+  h->cbar = h->hres[0];
+  h->have_target = true;
+  h->adjoint_valid = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_solid_primal_solve(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *info) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  lbm_status st = check_opts(h, o);
+  if (st) return st;
+  h->adjoint_valid = false;
+  h->adj_warm = false;
+  auto sweep = [h](bool mon) { return primal_sweep(h, mon); };
+  auto resid = [h](double &v) { return residual(h, h->fcur, h->fnext, v); };
+  return solve_loop(h, o, info, sweep, resid, false);
+}
+
+lbm_status lbm_solid_objective(lbm_solid *h, double *J) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!J) return fail(h, LBM_ERR_ARG, "J is NULL");
+  if (!h->have_target) return fail(h, LBM_ERR_STATE, "objective needs set_target first");
+  lbm_status st = objective_partials(h);
+  if (st) return st;
+  if ((st = finish(h, h->nblocks2d, 1, 0, 0.5 * h->dx * h->dx / h->cbar, h->dres))) return st;
+  if ((st = fetch(h, 1))) return st;
+  *J = h->hres[0];
+  return LBM_OK;
+}
+
+lbm_status lbm_solid_adjoint_solve(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *info) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  lbm_status st = check_opts(h, o);
+  if (st) return st;
+  if (!h->have_target) return fail(h, LBM_ERR_STATE, "adjoint needs set_target first");
+  // constant terms of Algorithm 1: r from the current primal state
+  if ((st = objective_partials(h))) return st;
+  if (!h->adj_warm) CK(h, cudaMemsetAsync(h->pcur, 0, sizeof(double) * 8 * h->N, h->stream));
+  h->adj_warm = false;
+  auto sweep = [h](bool mon) { return adjoint_sweep(h, mon); };
+  auto resid = [h](double &v) { return residual(h, h->pcur, h->pnext, v); };
+  st = solve_loop(h, o, info, sweep, resid, false);
+  if (st == LBM_OK || st == LBM_ERR_NOT_CONVERGED) h->adjoint_valid = true;
+  return st;
+}
+
+lbm_status lbm_solid_gradient(lbm_solid *h, double *grad, size_t n, int project) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!grad) return fail(h, LBM_ERR_ARG, "grad is NULL");
+  if (!h->adjoint_valid) return fail(h, LBM_ERR_STATE, "gradient needs an adjoint solve at the current primal state");
+  const double dx2 = h->dx * h->dx;
+  lbm_status st;
+  if (h->control == LBM_CTRL_FORCE_FIELD) {
+    if (n != (size_t)(2 * h->N)) return fail(h, LBM_ERR_ARG, "FORCE_FIELD gradient has 2N values");
+    if (h->periodic)
+      k_grad_force<false, 0><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, nullptr, grad, dx2, h->grid, h->bnd, h->partial);
+    else
+      k_grad_force<true, 0><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, nullptr, grad, dx2, h->grid, h->bnd, h->partial);
+    LAUNCHED(h);
+    if (project) {
+      if ((st = finish(h, h->nblocks2d, 2, 0, 1.0 / (double)h->n_active, h->dres))) return st;
+      if (h->periodic)
+        k_subtract_mean<false><<<h->grd, h->blk, 0, h->stream>>>(grad, h->dres, h->grid, h->bnd);
+      else
+        k_subtract_mean<true><<<h->grd, h->blk, 0, h->stream>>>(grad, h->dres, h->grid, h->bnd);
+      LAUNCHED(h);
+    }
+    return LBM_OK;
+  }
+  if (h->control == LBM_CTRL_FORCE_BASIS2) {
+    if (n != 2) return fail(h, LBM_ERR_ARG, "FORCE_BASIS2 gradient has 2 values");
+    if (h->periodic)
+      k_grad_force<false, 1><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, h->basis, nullptr, dx2, h->grid, h->bnd, h->partial);
+    else
+      k_grad_force<true, 1><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, h->basis, nullptr, dx2, h->grid, h->bnd, h->partial);
+    LAUNCHED(h);
+    return finish(h, h->nblocks2d, 2, 0, 1.0, grad);
+  }
+  return fail(h, LBM_ERR_ARG, "gradient for this control kind is not built");
+}
+
+lbm_status lbm_solid_get_populations(lbm_solid *h, int which, double *dst) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!dst) return fail(h, LBM_ERR_ARG, "dst is NULL");
+  const size_t pop = sizeof(double) * 8 * h->N;
+  if (which == 0) {
+    if (h->fcur_is_fs) {
+      CK(h, cudaMemcpyAsync(dst, h->fcur, pop, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      if (h->periodic)
+        k_pull_primal<false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, dst, h->grid, h->bnd);
+      else
+        k_pull_primal<true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, dst, h->grid, h->bnd);
+      LAUNCHED(h);
+    }
+    return LBM_OK;
+  }
+  if (which == 1) {
+    if (h->periodic)
+      k_pull_adjoint<false><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, dst, h->grid, h->bnd);
+    else
+      k_pull_adjoint<true><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, dst, h->grid, h->bnd);
+    LAUNCHED(h);
+    return LBM_OK;
+  }
+  if (which == 2) {
+    CK(h, cudaMemcpyAsync(dst, h->pcur, pop, cudaMemcpyDeviceToDevice, h->stream));
+    return LBM_OK;
+  }
+  return fail(h, LBM_ERR_ARG, "which must be 0, 1 or 2");
+}
+
+lbm_status lbm_solid_set_populations(lbm_solid *h, int which, const double *src) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!src) return fail(h, LBM_ERR_ARG, "src is NULL");
+  const size_t pop = sizeof(double) * 8 * h->N;
+  if (which == 0) {
+    CK(h, cudaMemcpyAsync(h->fcur, src, pop, cudaMemcpyDeviceToDevice, h->stream));
+    h->fcur_is_fs = true;
+    h->adjoint_valid = false;
+    return LBM_OK;
+  }
+  if (which == 2) {
+    CK(h, cudaMemcpyAsync(h->pcur, src, pop, cudaMemcpyDeviceToDevice, h->stream));
+    h->adj_warm = true;
+    return LBM_OK;
+  }
+  return fail(h, LBM_ERR_ARG, "which must be 0 (f_S) or 2 (phi_C)");
+}
+
+lbm_status lbm_solid_displacement(lbm_solid *h, double *d) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!d) return fail(h, LBM_ERR_ARG, "d is NULL");
+  if (h->periodic) {
+    if (h->fcur_is_fs)
+      k_displacement<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, d, h->grid, h->bnd);
+    else
+      k_displacement<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, d, h->grid, h->bnd);
+  } else {
+    if (h->fcur_is_fs)
+      k_displacement<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, d, h->grid, h->bnd);
+    else
+      k_displacement<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, d, h->grid, h->bnd);
+  }
+  LAUNCHED(h);
+  return LBM_OK;
+}
+
+}  // extern "C"

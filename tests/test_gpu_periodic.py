@@ -1,0 +1,225 @@
+"""GPU parity of the periodic path against the CPU oracle, through the C ABI.
+
+Tolerances (fixed before any kernel ran): populations after a fixed step count
+within 1e-11 relative L-inf, gradients within 1e-10 relative L-inf (relative to the
+largest entry of the oracle's array).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_31347_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-11
+GRAD_TOL = 1e-10
+
+
+def rel_inf(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def lbm_mod():
+    from paper_2609_31347_b300 import lbm
+    assert torch.cuda.is_available()
+    lbm.load_library()
+    return lbm
+
+
+# (nx, ny, E, nu, steps): tiny wraps, ragged tiles, several blocks in x and y
+CASES = [(3, 3, 1.0, 0.3, 7), (4, 5, 0.11, 0.8, 20), (7, 3, 0.5, -0.2, 13),
+         (33, 17, 0.11, 0.8, 40), (130, 67, 2.0, 0.25, 25), (257, 9, 0.7, 0.1, 11)]
+
+
+def periodic_problem(nx, ny, seed):
+    F = I.fourier_force(nx, ny=ny, seed=seed, kmax=2)
+    rng = np.random.default_rng(seed + 100)
+    dstar = rng.standard_normal((2, nx * ny)) * 1e-3
+    return F, dstar
+
+
+@pytest.mark.parametrize("nx,ny,E,nu,steps", CASES)
+def test_primal_adjoint_gradient_match_the_oracle(lbm_mod, nx, ny, E, nu, steps):
+    F, dstar = periodic_problem(nx, ny, seed=nx + ny)
+    dx = 1.0 / nx
+    s = lbm_mod.LBMSolid(nx, ny, dx, E, nu, periodic=True, control="force_field")
+    s.set_target(dev(dstar))
+    s.set_control(dev(F))
+    s.primal_solve(steps, fixed_steps=True)
+    fS_gpu = host(s.get_populations(0)).reshape(8, -1)
+    g = oracle.Grid(nx, ny, dx, nu)
+    fS = oracle.primal(g, E, F, steps)
+    assert rel_inf(fS_gpu, fS) <= POP_TOL
+    d_gpu = host(s.displacement()).reshape(2, -1)
+    assert rel_inf(d_gpu, oracle.displacement(g, fS, F)) <= POP_TOL
+    J_gpu = s.objective()
+    J, _ = oracle.objective(g, fS, F, dstar)
+    assert abs(J_gpu - J) <= 1e-12 * abs(J)
+    K = steps + 3
+    s.adjoint_solve(K, fixed_steps=True)
+    phiC, phiS = oracle.adjoint(g, E, F, fS, dstar, K)
+    assert rel_inf(host(s.get_populations(2)).reshape(8, -1), phiC) <= POP_TOL
+    assert rel_inf(host(s.get_populations(1)).reshape(8, -1), phiS) <= POP_TOL
+    grad = host(s.gradient()).reshape(2, -1)
+    gref = oracle.gradient_force(g, E, F, fS, phiS, dstar)
+    assert rel_inf(grad, gref) <= GRAD_TOL
+    gproj = host(s.gradient(project_zero_mean=True)).reshape(2, -1)
+    assert rel_inf(gproj, gref - gref.mean(axis=1, keepdims=True)) <= GRAD_TOL
+    s.close()
+
+
+def test_benchmark1_basis_gradient_matches_fad(lbm_mod):
+    # F = alpha o F* (Eq. control_param_periodic) at alpha = (-1, -1), N_x = 20: the ALBM
+    # gradient on the GPU equals the oracle's f-AD derivative (converged states).
+    nx = 20
+    m = I.periodic_manufactured(nx)
+    basis = I.paper_scale_basis(m["Fstar"])
+    s = lbm_mod.LBMSolid(nx, nx, m["dx"], I.PAPER_E, I.PAPER_NU, control="force_basis2",
+                         force_basis=basis.reshape(-1))
+    s.set_target(dev(m["dstar"]))
+    s.set_control(dev([-1.0, -1.0]))
+    steps = 30 * nx * nx
+    s.primal_solve(steps, fixed_steps=True)
+    s.adjoint_solve(steps, fixed_steps=True)
+    g_gpu = host(s.gradient())
+    g = oracle.Grid(nx, nx, m["dx"], I.PAPER_NU)
+    F = -m["Fstar"]
+    for i in range(2):
+        fSv, fSd = oracle.primal_tangent(g, I.PAPER_E, F, steps, Fdot=basis[i])
+        _, Jd = oracle.objective_tangent(g, fSv, fSd, F, m["dstar"], Fdot=basis[i])
+        assert abs(g_gpu[i] - Jd) <= 1e-10 * abs(Jd)
+    s.close()
+
+
+def test_tiled_force_at_bench_size(lbm_mod):
+    # Sampled parity at 4096^2 in the benchmark's launch configuration: a force with
+    # period 16 gives a 16-periodic state (translation invariance), so every node of
+    # the 4096^2 run must equal the 16^2 oracle run at the same position modulo 16.
+    P, nx = 16, 4096
+    Fp = I.fourier_force(P, seed=11, kmax=3).reshape(2, P, P)
+    reps = nx // P
+    F = np.tile(Fp, (1, reps, reps)).reshape(2, -1)
+    rng = np.random.default_rng(12)
+    dp = rng.standard_normal((2, P, P)) * 1e-3
+    dstar = np.tile(dp, (1, reps, reps)).reshape(2, -1)
+    E, nu, steps = 0.11, 0.8, 6
+    dx = 1.0 / nx
+    s = lbm_mod.LBMSolid(nx, nx, dx, E, nu, control="force_field")
+    s.set_target(dev(dstar))
+    s.set_control(dev(F))
+    s.primal_solve(steps, fixed_steps=True)
+    fS_gpu = s.get_populations(0).view(8, nx, nx)
+    g = oracle.Grid(P, P, dx, nu)
+    fS = oracle.primal(g, E, Fp.reshape(2, -1), steps).reshape(8, P, P)
+    rows = torch.tensor([0, 1, 15, 16, 2047, 4080, 4095], device="cuda")
+    sub = host(fS_gpu[:, rows][:, :, :]).reshape(8, len(rows), nx)
+    ref = fS[:, host(rows) % P][:, :, np.arange(nx) % P]
+    assert rel_inf(sub, ref) <= POP_TOL
+    K = 5
+    s.adjoint_solve(K, fixed_steps=True)
+    _, phiS = oracle.adjoint(g, E, Fp.reshape(2, -1), fS.reshape(8, -1), dp.reshape(2, -1), K)
+    # the objective normalisation Cbar scales with the number of tiles
+    phiS = phiS / (reps * reps)
+    ps_gpu = s.get_populations(1).view(8, nx, nx)
+    sub = host(ps_gpu[:, rows]).reshape(8, len(rows), nx)
+    ref = phiS.reshape(8, P, P)[:, host(rows) % P][:, :, np.arange(nx) % P]
+    assert rel_inf(sub, ref) <= POP_TOL
+    s.close()
+
+
+def test_stopping_rules_and_status_codes(lbm_mod):
+    nx = 16
+    m = I.periodic_manufactured(nx)
+    s = lbm_mod.LBMSolid(nx, nx, m["dx"], I.PAPER_E, I.PAPER_NU)
+    s.set_control(dev(m["Fstar"]))
+    # residual rule (criterion 1) reaches 1e-12 well before 30 N_x^2 steps
+    info = s.primal_solve(30 * nx * nx, tol=1e-12, criterion=1, check_every=64)
+    assert info.status == lbm_mod.LBM_OK and info.steps < 30 * nx * nx and info.last_metric < 1e-12
+    # the converged state matches the exact fixed point
+    from oracle import fourier
+    fF = fourier.periodic_fixed_point(nx, I.PAPER_E, I.PAPER_NU, m["Fstar"])
+    assert rel_inf(host(s.get_populations(0)).reshape(8, -1), fF) <= 1e-9
+    # CV rule of Eq. convergence_crit (paper): window of samples of c(t)
+    s.set_control(dev(m["Fstar"]))
+    info = s.primal_solve(100 * nx * nx, tol=1e-7, criterion=0, window=100,
+                          check_every=max(1, nx * nx // 100))
+    assert info.status == lbm_mod.LBM_OK and info.last_metric < 1e-7
+    # not converged within the cap
+    s.set_control(dev(m["Fstar"]))
+    info = s.primal_solve(50, tol=1e-14, criterion=1, check_every=10, allow_not_converged=True)
+    assert info.status == lbm_mod.LBM_ERR_NOT_CONVERGED and info.steps == 50
+    # out-of-order calls
+    with pytest.raises(lbm_mod.LBMError) as e:
+        s.objective()
+    assert e.value.status == lbm_mod.LBM_ERR_STATE
+    s.set_target(dev(m["dstar"]))
+    with pytest.raises(lbm_mod.LBMError) as e:
+        s.gradient()
+    assert e.value.status == lbm_mod.LBM_ERR_STATE
+    with pytest.raises(lbm_mod.LBMError) as e:
+        s.set_control(dev(np.zeros(3)))
+    assert e.value.status == lbm_mod.LBM_ERR_ARG
+    s.close()
+
+
+def test_divergence_is_reported(lbm_mod):
+    nx = 8
+    s = lbm_mod.LBMSolid(nx, nx, 1.0 / nx, 1.0, 0.3)
+    F = np.zeros((2, nx * nx))
+    F[0, 3] = np.inf
+    s.set_control(dev(F))
+    info = s.primal_solve(100, tol=1e-10, criterion=0, window=4, check_every=5,
+                          allow_not_converged=True)
+    assert info.status == lbm_mod.LBM_ERR_DIVERGED
+    s.close()
+
+
+def test_warm_start_and_checkpoint_roundtrip(lbm_mod):
+    nx, steps = 12, 40
+    F, dstar = periodic_problem(nx, nx, seed=5)
+    s = lbm_mod.LBMSolid(nx, nx, 1.0 / nx, 0.4, 0.2)
+    s.set_control(dev(F))
+    s.primal_solve(steps, fixed_steps=True)
+    ck = s.get_populations(0).clone()
+    s.primal_solve(steps, fixed_steps=True)
+    full = host(s.get_populations(0))
+    # restart from the checkpoint: same result as the uninterrupted run
+    s.set_control(dev(F))
+    s.set_populations(0, ck)
+    s.primal_solve(steps, fixed_steps=True)
+    assert np.array_equal(host(s.get_populations(0)), full)
+    # keep_state continues from the current state
+    s.set_control(dev(F))
+    s.primal_solve(steps, fixed_steps=True)
+    s.set_control(dev(F), keep_state=True)
+    s.primal_solve(steps, fixed_steps=True)
+    assert np.array_equal(host(s.get_populations(0)), full)
+    s.close()
+
+
+def test_deterministic_reductions(lbm_mod):
+    nx = 300
+    F, dstar = periodic_problem(nx, nx, seed=9)
+    s = lbm_mod.LBMSolid(nx, nx, 1.0 / nx, 0.3, 0.3)
+    s.set_target(dev(dstar))
+    out = []
+    for _ in range(2):
+        s.set_control(dev(F))
+        s.primal_solve(20, fixed_steps=True)
+        J = s.objective()
+        s.adjoint_solve(20, fixed_steps=True)
+        out.append((J, host(s.gradient(project_zero_mean=True))))
+    assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
+    s.close()
