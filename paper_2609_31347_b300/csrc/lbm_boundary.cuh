@@ -28,69 +28,103 @@ struct BoundaryNode {
   double nrm[2];    // outward unit normal
 };
 
-struct Material {
-  double w11, ws, wd, K;
+// Forward-mode dual number: the setup kernel evaluates each rule with the modulus
+// seeded (dE = 1) to get dQ/dE and ds/dE for the Young's-modulus gradient.
+struct Dual {
+  double v, d;
+  __device__ Dual(double a = 0.0, double b = 0.0) : v(a), d(b) {}
 };
-
-__device__ inline void neumann_2p(const double (&fc)[8], double Tx, double Ty, double nx_,
-                                  double ny_, const Material &m, double dx, double (&p2)[8]) {
-  // post-collision even moments of the node
-  const double mc11 = fc[4] - fc[5] + fc[6] - fc[7];
-  const double mcs = fc[0] + fc[1] + fc[2] + fc[3] + 2.0 * (fc[4] + fc[5] + fc[6] + fc[7]);
-  const double mcd = fc[0] - fc[1] + fc[2] - fc[3];
-  const double b11 = mc11 * (2.0 - m.w11) / (2.0 * (1.0 - m.w11));
-  const double bs = mcs * (2.0 - m.ws) / (2.0 * (1.0 - m.ws));
-  const double bd = mcd * (2.0 - m.wd) / (2.0 * (1.0 - m.wd));
-  const double s11 = -0.5 * (bs + bd) / dx, s22 = -0.5 * (bs - bd) / dx, s12 = -b11 / dx;
-  const double rx = Tx - (s11 * nx_ + s12 * ny_);
-  const double ry = Ty - (s12 * nx_ + s22 * ny_);
-  const double rn = rx * nx_ + ry * ny_;
-  const double w11 = s11 + 2.0 * rx * nx_ - rn * nx_ * nx_;
-  const double w22 = s22 + 2.0 * ry * ny_ - rn * ny_ * ny_;
-  const double w12 = s12 + rx * ny_ + ry * nx_ - rn * nx_ * ny_;
-  const double m11 = -dx * w12, ms = -dx * (w11 + w22), md = -dx * (w11 - w22);
-  const double m22 = kTheta * ms / (4.0 * m.K);
-  // 2 p = 2 M^-1 (0, 0, m11, ms, md, 0, 0, m22)
-  p2[0] = p2[2] = 0.5 * (ms + md) - m22;
-  p2[1] = p2[3] = 0.5 * (ms - md) - m22;
-  p2[4] = p2[6] = 0.5 * (m22 + m11);
-  p2[5] = p2[7] = 0.5 * (m22 - m11);
+__device__ inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__device__ inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__device__ inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__device__ inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ inline Dual operator/(Dual a, Dual b) {
+  return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
 }
 
-__device__ inline double boundary_rule(const BoundaryNode &bn, int k, const double (&fc)[8],
-                                       bool with_data, const Material &m, double dx) {
+// Material seen by the boundary rules: omega of m11, m_s, m_d and K, with their
+// derivatives with respect to E (d = 0 when no derivative is wanted).
+struct Material {
+  double w11, ws, wd, K;
+  double dw11, dws, dwd, dK;
+};
+
+template <class T>
+__device__ inline void neumann_2p(const T (&fc)[8], T Tx, T Ty, double nx_, double ny_,
+                                  const T (&w)[3], T K, double dx, T (&p2)[8]) {
+  const T one(1.0), two(2.0), half(0.5);
+  // post-collision even moments of the node
+  const T mc11 = fc[4] - fc[5] + fc[6] - fc[7];
+  const T mcs = fc[0] + fc[1] + fc[2] + fc[3] + two * (fc[4] + fc[5] + fc[6] + fc[7]);
+  const T mcd = fc[0] - fc[1] + fc[2] - fc[3];
+  const T b11 = mc11 * (two - w[0]) / (two * (one - w[0]));
+  const T bs = mcs * (two - w[1]) / (two * (one - w[1]));
+  const T bd = mcd * (two - w[2]) / (two * (one - w[2]));
+  const T idx(1.0 / dx), nX(nx_), nY(ny_);
+  const T s11 = -(half * (bs + bd)) * idx, s22 = -(half * (bs - bd)) * idx, s12 = -b11 * idx;
+  const T rx = Tx - (s11 * nX + s12 * nY);
+  const T ry = Ty - (s12 * nX + s22 * nY);
+  const T rn = rx * nX + ry * nY;
+  const T w11 = s11 + two * rx * nX - rn * nX * nX;
+  const T w22 = s22 + two * ry * nY - rn * nY * nY;
+  const T w12 = s12 + rx * nY + ry * nX - rn * nX * nY;
+  const T mdx(-dx);
+  const T m11 = mdx * w12, ms = mdx * (w11 + w22), md = mdx * (w11 - w22);
+  const T m22 = T(kTheta) * ms / (T(4.0) * K);
+  // 2 p = 2 M^-1 (0, 0, m11, ms, md, 0, 0, m22)
+  p2[0] = p2[2] = half * (ms + md) - m22;
+  p2[1] = p2[3] = half * (ms - md) - m22;
+  p2[4] = p2[6] = half * (m22 + m11);
+  p2[5] = p2[7] = half * (m22 - m11);
+}
+
+template <class T>
+__device__ inline T boundary_rule(const BoundaryNode &bn, int k, const T (&fc)[8],
+                                  bool with_data, const T (&w)[3], T K, double dx) {
   const int cx[8] = {1, 0, -1, 0, 1, -1, -1, 1};
   const int cy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
   const int kb = (k < 4) ? ((k + 2) & 3) : (((k - 4 + 2) & 3) + 4);
   if (bn.code[k] == 1) {
-    const double w = k < 4 ? (1.0 - kTheta) : 0.5 * kTheta;
-    const double src = with_data ? w * (cx[k] * bn.wd[0] + cy[k] * bn.wd[1]) : 0.0;
-    return fc[kb] + src;
+    const double wk = k < 4 ? (1.0 - kTheta) : 0.5 * kTheta;
+    const double src = with_data ? wk * (cx[k] * bn.wd[0] + cy[k] * bn.wd[1]) : 0.0;
+    return fc[kb] + T(src);
   }
-  double p2[8];
-  neumann_2p(fc, with_data ? bn.T[0] : 0.0, with_data ? bn.T[1] : 0.0, bn.nrm[0], bn.nrm[1], m,
-             dx, p2);
+  T p2[8];
+  neumann_2p(fc, T(with_data ? bn.T[0] : 0.0), T(with_data ? bn.T[1] : 0.0), bn.nrm[0],
+             bn.nrm[1], w, K, dx, p2);
   return -fc[kb] + p2[k];
 }
 
-// One thread per boundary record: Q (row-major [k*8+j]) and s.
+// One thread per boundary record: Q (row-major [k*8+j]) and s, and their derivatives
+// with respect to E (dQ, ds; skipped when dQ == nullptr).
 __global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, long nb, Material m,
-                                 double dx, double *__restrict__ Q, double *__restrict__ s) {
+                                 double dx, double *__restrict__ Q, double *__restrict__ s,
+                                 double *__restrict__ dQ, double *__restrict__ ds) {
   const long b = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const BoundaryNode bn = nodes[b];
-  double zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const Dual w[3] = {Dual(m.w11, m.dw11), Dual(m.ws, m.dws), Dual(m.wd, m.dwd)};
+  const Dual K(m.K, m.dK);
   for (int k = 0; k < 8; ++k) {
     if (bn.code[k] == 0) {
       s[b * 8 + k] = 0.0;
-      for (int j = 0; j < 8; ++j) Q[b * 64 + k * 8 + j] = 0.0;
+      if (dQ) ds[b * 8 + k] = 0.0;
+      for (int j = 0; j < 8; ++j) {
+        Q[b * 64 + k * 8 + j] = 0.0;
+        if (dQ) dQ[b * 64 + k * 8 + j] = 0.0;
+      }
       continue;
     }
-    s[b * 8 + k] = boundary_rule(bn, k, zero, true, m, dx);
+    Dual zero[8];
+    const Dual r0 = boundary_rule(bn, k, zero, true, w, K, dx);
+    s[b * 8 + k] = r0.v;
+    if (dQ) ds[b * 8 + k] = r0.d;
     for (int j = 0; j < 8; ++j) {
-      double e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      e[j] = 1.0;
-      Q[b * 64 + k * 8 + j] = boundary_rule(bn, k, e, false, m, dx);
+      Dual e[8];
+      e[j] = Dual(1.0, 0.0);
+      const Dual r = boundary_rule(bn, k, e, false, w, K, dx);
+      Q[b * 64 + k * 8 + j] = r.v;
+      if (dQ) dQ[b * 64 + k * 8 + j] = r.d;
     }
   }
 }

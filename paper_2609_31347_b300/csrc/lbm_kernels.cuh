@@ -30,6 +30,13 @@ struct Bounded {
   const double *Q;        // nb * 64, row-major Q[k*8+j]
   const double *s;        // nb * 8
   const uint8_t *regmask; // nb: bit k set <=> link k (incoming) is regular
+  const double *dQ;       // nb * 64: dQ/dE (Young's-modulus controls only)
+  const double *ds;       // nb * 8:  ds/dE
+};
+
+// Derivatives of the collision constants with respect to E (c = 1 - omega).
+struct YoungDeriv {
+  double dc11, dcs, dcd, dgam;
 };
 
 // Neighbour index with periodic wrap.
@@ -371,6 +378,58 @@ __global__ void __launch_bounds__(256) k_grad_force(const double *__restrict__ p
     partial[bl * 2 + 0] = acc[0];
     partial[bl * 2 + 1] = acc[1];
   }
+}
+
+// Young's-modulus gradient (Eq. optimality with E entering omega_beta(E) and, at
+// boundary nodes, gamma(E) and the Neumann rule):
+//   dJ/dE = - sum_n phi_S,n^T dC_n/dE - sum_n phi_C,n^T (dS'/dE f_C)_n,
+// with J free of E (the loads are held fixed) and dC_n/dE read off the pair form:
+// c11 scales m11/4 on the diagonals (+,-,+,-), cs scales m_s on the axis pairs
+// (1/4 + gamma/2) and on the diagonals (-gamma/4), cd scales m_d/4 on the axis pairs
+// (+,-,+,-), gamma scales cs m_s (1/2 on axis, -1/4 on diagonals).
+template <bool BOUNDED>
+__global__ void __launch_bounds__(256) k_grad_young(const double *__restrict__ fin,
+                                                    const double *__restrict__ pin, Grid g,
+                                                    Bounded b, Coef c, YoungDeriv yd,
+                                                    double *__restrict__ partial) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  double acc[1] = {0.0};
+  if (x < g.nx && y < g.ny) {
+    const long n = (long)y * g.nx + x;
+    double f[8], p[8], gsel, gsel2;
+    if (pull_primal<BOUNDED>(fin, x, y, g, b, f, gsel) &&
+        pull_adjoint<BOUNDED>(pin, x, y, g, b, p, gsel2)) {
+      const double m11 = (f[4] + f[6]) - (f[5] + f[7]);
+      const double ms = (f[0] + f[1] + f[2] + f[3]) + 2.0 * (f[4] + f[5] + f[6] + f[7]);
+      const double md = (f[0] + f[2]) - (f[1] + f[3]);
+      const double pax = p[0] + p[1] + p[2] + p[3], pdg = p[4] + p[5] + p[6] + p[7];
+      const bool bnd = BOUNDED && gsel != 0.0;
+      const double gam = bnd ? c.gam : 0.0;
+      double t = yd.dc11 * 0.25 * m11 * ((p[4] + p[6]) - (p[5] + p[7]));
+      t += yd.dcd * 0.25 * md * ((p[0] + p[2]) - (p[1] + p[3]));
+      t += yd.dcs * ms * ((0.25 + 0.5 * gam) * pax - 0.25 * gam * pdg);
+      if (bnd) {
+        t += yd.dgam * c.cs * ms * (0.5 * pax - 0.25 * pdg);
+        const int bi = b.bidx[n];
+        const unsigned reg = b.regmask[bi];
+        double own[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) own[j] = __ldg(fin + j * g.N + n);
+        for (int k = 0; k < 8; ++k) {
+          if (reg & (1u << k)) continue;
+          double ds_ = b.ds[(long)bi * 8 + k];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) ds_ += b.dQ[(long)bi * 64 + k * 8 + j] * own[j];
+          t += __ldg(pin + k * g.N + n) * ds_;
+        }
+      }
+      acc[0] = -t;
+    }
+  }
+  __shared__ double sm[32];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
 }
 
 // Subtract per-component means over active nodes (Eq. zero_mean_projection).

@@ -37,7 +37,9 @@ struct lbm_solid {
   double *basis = nullptr, *Fbase = nullptr;
   uint8_t *type = nullptr, *regmask = nullptr;
   int *bidx = nullptr;
-  double *Q = nullptr, *s = nullptr;
+  double *Q = nullptr, *s = nullptr, *dQ = nullptr, *ds = nullptr;
+  YoungDeriv yd{};
+  double alpha = 0.0;  // scalar Young control (E = alpha^2)
   BoundaryNode *bnodes = nullptr;
   long nb = 0;
   double *partial = nullptr;
@@ -86,7 +88,7 @@ constexpr double kTh = 1.0 / 3.0;
 
 // Material map (Eqs. lambda, mu, K) and relaxation (Table A.1, Eq. relaxation, Eq. gamma).
 bool material_coefs(double E, double nu, bool bounded, bool neumann, Coef &c, Material &m,
-                    std::string &why) {
+                    YoungDeriv &yd, std::string &why) {
   if (!(E > 0.0) || !std::isfinite(E)) { why = "Young's modulus must be > 0"; return false; }
   if (!(nu > -1.0 && nu < 1.0)) { why = "Poisson ratio must lie in (-1, 1)"; return false; }
   const double mu = E / (2.0 * (1.0 + nu));
@@ -107,7 +109,13 @@ bool material_coefs(double E, double nu, bool bounded, bool neumann, Coef &c, Ma
   c.q11 = 0.25 * c.c11; c.qs = 0.25 * c.cs; c.qd = 0.25 * c.cd;
   c.qs_b = c.cs * (0.25 + 0.5 * c.gam);
   c.P_b = -0.25 * c.gam * c.cs;
+  // derivatives with respect to E: d omega = -omega^2 d tau
+  const double dmu = 1.0 / (2.0 * (1.0 + nu)), dK = 1.0 / (2.0 * (1.0 - nu));
+  const double dt11 = dmu / kTh, dts = 2.0 * dK / (1.0 + kTh), dtd = 2.0 * dmu / (1.0 - kTh);
   m.w11 = w11; m.ws = ws; m.wd = wd; m.K = K;
+  m.dw11 = -w11 * w11 * dt11; m.dws = -ws * ws * dts; m.dwd = -wd * wd * dtd; m.dK = dK;
+  yd.dc11 = -m.dw11; yd.dcs = -m.dws; yd.dcd = -m.dwd;
+  yd.dgam = bounded ? -kTh * 0.5 * dts / ((1.0 + kTh) * (ts - 0.5) * (ts - 0.5)) : 0.0;
   return true;
 }
 
@@ -115,7 +123,8 @@ lbm_status setup_boundary(lbm_solid *h) {
   if (h->periodic || h->nb == 0) return LBM_OK;
   const unsigned threads = 128;
   const unsigned blocks = (unsigned)((h->nb + threads - 1) / threads);
-  k_boundary_setup<<<blocks, threads, 0, h->stream>>>(h->bnodes, h->nb, h->mat, h->dx, h->Q, h->s);
+  k_boundary_setup<<<blocks, threads, 0, h->stream>>>(h->bnodes, h->nb, h->mat, h->dx, h->Q, h->s,
+                                                      h->dQ, h->ds);
   LAUNCHED(h);
   return LBM_OK;
 }
@@ -123,12 +132,14 @@ lbm_status setup_boundary(lbm_solid *h) {
 lbm_status set_material(lbm_solid *h, double E) {
   Coef c{};
   Material m{};
+  YoungDeriv yd{};
   std::string why;
-  if (!material_coefs(E, h->nu, !h->periodic, h->has_neumann, c, m, why))
+  if (!material_coefs(E, h->nu, !h->periodic, h->has_neumann, c, m, yd, why))
     return fail(h, LBM_ERR_ARG, why);
   c.dx = h->dx;
   h->coef = c;
   h->mat = m;
+  h->yd = yd;
   h->E = E;
   return setup_boundary(h);
 }
@@ -295,7 +306,8 @@ lbm_status objective_partials(lbm_solid *h) {
 
 void free_all(lbm_solid *h) {
   void *bufs[] = {h->fA, h->fB, h->pA, h->pB, h->g2, h->r2, h->dstar, h->obs, h->basis, h->Fbase,
-                  h->type, h->regmask, h->bidx, h->Q, h->s, h->bnodes, h->partial, h->dres};
+                  h->type, h->regmask, h->bidx, h->Q, h->s, h->dQ, h->ds, h->bnodes,
+                  h->partial, h->dres};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (h->hres) cudaFreeHost(h->hres);
@@ -422,6 +434,10 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
       ALLOC(h->bnodes, sizeof(BoundaryNode) * h->nb);
       ALLOC(h->Q, sizeof(double) * 64 * h->nb);
       ALLOC(h->s, sizeof(double) * 8 * h->nb);
+      if (d->control >= LBM_CTRL_YOUNG_SCALAR) {
+        ALLOC(h->dQ, sizeof(double) * 64 * h->nb);
+        ALLOC(h->ds, sizeof(double) * 8 * h->nb);
+      }
     }
   }
 #undef ALLOC
@@ -449,7 +465,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
       up(h->regmask, regm.data(), h->nb);
       up(h->bnodes, bn.data(), sizeof(BoundaryNode) * h->nb);
     }
-    h->bnd = Bounded{h->type, h->bidx, h->Q, h->s, h->regmask};
+    h->bnd = Bounded{h->type, h->bidx, h->Q, h->s, h->regmask, h->dQ, h->ds};
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->fA, 0, pop, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->fB, 0, pop, h->stream);
@@ -514,6 +530,7 @@ lbm_status lbm_solid_set_control(lbm_solid *h, const double *alpha, size_t n, in
       CK(h, cudaStreamSynchronize(h->stream));
       const lbm_status st = set_material(h, h->hres[0] * h->hres[0]);
       if (st) return st;
+      h->alpha = h->hres[0];
       break;
     }
     default:
@@ -625,6 +642,17 @@ lbm_status lbm_solid_gradient(lbm_solid *h, double *grad, size_t n, int project)
       k_grad_force<true, 1><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, h->basis, nullptr, dx2, h->grid, h->bnd, h->partial);
     LAUNCHED(h);
     return finish(h, h->nblocks2d, 2, 0, 1.0, grad);
+  }
+  if (h->control == LBM_CTRL_YOUNG_SCALAR) {
+    if (n != 1) return fail(h, LBM_ERR_ARG, "YOUNG_SCALAR gradient has 1 value");
+    if (h->fcur_is_fs) return fail(h, LBM_ERR_STATE, "Young gradient needs a primal solve");
+    if (h->periodic)
+      k_grad_young<false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->partial);
+    else
+      k_grad_young<true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->partial);
+    LAUNCHED(h);
+    // E = alpha^2 (Eq. E_substitution): dJ/dalpha = 2 alpha dJ/dE
+    return finish(h, h->nblocks2d, 1, 0, 2.0 * h->alpha, grad);
   }
   return fail(h, LBM_ERR_ARG, "gradient for this control kind is not built");
 }

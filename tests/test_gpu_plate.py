@@ -1,0 +1,137 @@
+"""GPU parity of the bounded (elliptic plate) path against the CPU oracle, through the
+C ABI: the boundary rules, their transpose in the adjoint sweep, the force gradient and
+the Young's-modulus gradient (E = alpha^2, Section 4.3.3).
+
+Tolerances as for the periodic path: 1e-11 relative L-inf on populations after a fixed
+step count, 1e-10 on gradients.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_31347_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-11
+GRAD_TOL = 1e-10
+
+
+def rel_inf(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def lbm_mod():
+    from paper_2609_31347_b300 import lbm
+    assert torch.cuda.is_available()
+    lbm.load_library()
+    return lbm
+
+
+def paper_plate(Nx, E=I.PLATE_E, nu=I.PLATE_NU):
+    geo = I.plate_geometry(Nx)
+    dstar, sigma, F = I.plate_manufactured(geo.X, geo.Y, E=E, nu=nu)
+    wd, wT = I.plate_wall_data(geo, dstar, sigma)
+    return geo, dstar, F * geo.active, wd, wT
+
+
+def make(lbm_mod, geo, wd, wT, E, nu, control="force_field", force=None):
+    return lbm_mod.LBMSolid(geo.nx, geo.nx, geo.dx, E, nu, periodic=False,
+                            node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
+                            wall_n=geo.normal, obs=geo.active.astype(float), control=control,
+                            force=force)
+
+
+def ogrid(geo, wd, wT, nu):
+    return oracle.Grid(geo.nx, geo.nx, geo.dx, nu, periodic=False, node_type=geo.node_type,
+                       link=geo.link, wall_d=wd, wall_T=wT, wall_n=geo.normal)
+
+
+@pytest.mark.parametrize("Nx,E,nu,steps", [(12, I.PLATE_E, I.PLATE_NU, 30),
+                                           (20, 1.0, 0.3, 45), (37, 0.15, 0.7, 23)])
+def test_plate_primal_adjoint_force_gradient(lbm_mod, Nx, E, nu, steps):
+    geo, dstar, F, wd, wT = paper_plate(Nx, E=E, nu=nu)
+    s = make(lbm_mod, geo, wd, wT, E, nu)
+    s.set_target(dev(dstar))
+    s.set_control(dev(F))
+    s.primal_solve(steps, fixed_steps=True)
+    g = ogrid(geo, wd, wT, nu)
+    fS = oracle.primal(g, E, F, steps)
+    assert rel_inf(host(s.get_populations(0)).reshape(8, -1), fS) <= POP_TOL
+    obs = geo.active.astype(float)
+    J, _ = oracle.objective(g, fS, F, dstar, obs=obs)
+    assert abs(s.objective() - J) <= 1e-12 * abs(J)
+    K = steps + 5
+    s.adjoint_solve(K, fixed_steps=True)
+    phiC, phiS = oracle.adjoint(g, E, F, fS, dstar, K, obs=obs)
+    assert rel_inf(host(s.get_populations(2)).reshape(8, -1), phiC) <= POP_TOL
+    assert rel_inf(host(s.get_populations(1)).reshape(8, -1), phiS) <= POP_TOL
+    gref = oracle.gradient_force(g, E, F, fS, phiS, dstar, obs=obs)
+    assert rel_inf(host(s.gradient()).reshape(2, -1), gref) <= GRAD_TOL
+    # projection over active nodes only
+    act = geo.active == 1
+    gp = gref.copy()
+    gp[:, act] -= gref[:, act].mean(axis=1, keepdims=True)
+    assert rel_inf(host(s.gradient(project_zero_mean=True)).reshape(2, -1), gp) <= GRAD_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,E0", [(12, 0.15), (16, 0.07)])
+def test_plate_young_gradient_matches_oracle_and_fad(lbm_mod, Nx, E0):
+    # Benchmark (3): E = alpha^2 with loads fixed at the reference modulus (E* = 0.1)
+    geo, dstar, F, wd, wT = paper_plate(Nx)
+    s = make(lbm_mod, geo, wd, wT, I.PLATE_E, I.PLATE_NU, control="young_scalar", force=F)
+    s.set_target(dev(dstar))
+    alpha = np.sqrt(E0)
+    s.set_control(dev([alpha]))
+    steps = 20000
+    s.primal_solve(steps, fixed_steps=True)
+    s.adjoint_solve(steps, fixed_steps=True)
+    g_gpu = host(s.gradient())[0]
+    g = ogrid(geo, wd, wT, I.PLATE_NU)
+    obs = geo.active.astype(float)
+    fS = oracle.primal(g, E0, F, steps)
+    phiC, phiS = oracle.adjoint(g, E0, F, fS, dstar, steps, obs=obs)
+    _, dJdE = oracle.gradient_young(g, E0, F, fS, phiS, phiC)
+    assert abs(g_gpu - 2 * alpha * dJdE) <= GRAD_TOL * abs(2 * alpha * dJdE)
+    fSv, fSd = oracle.primal_tangent(g, E0, F, steps, Edot=1.0)
+    _, Jd = oracle.objective_tangent(g, fSv, fSd, F, dstar, obs=obs)
+    assert abs(g_gpu - 2 * alpha * Jd) <= 1e-9 * abs(2 * alpha * Jd)
+    s.close()
+
+
+def test_baseline_plate_geometry(lbm_mod):
+    # clamped-left / uniform-tension plate (zero body force), parity after fixed steps
+    geo, wd, wT = I.baseline_plate(40)
+    E, nu, steps = 1.0, 0.3, 50
+    s = make(lbm_mod, geo, wd, wT, E, nu)
+    s.set_control(dev(np.zeros((2, geo.nx * geo.nx))))
+    s.primal_solve(steps, fixed_steps=True)
+    g = ogrid(geo, wd, wT, nu)
+    fS = oracle.primal(g, E, np.zeros((2, geo.nx * geo.nx)), steps)
+    assert rel_inf(host(s.get_populations(0)).reshape(8, -1), fS) <= POP_TOL
+    s.close()
+
+
+def test_plate_rejects_inconsistent_links(lbm_mod):
+    geo, dstar, F, wd, wT = paper_plate(12)
+    bad = geo.link.copy()
+    n = int(np.where(geo.node_type == 2)[0][0])
+    k = int(np.where(bad[:, n] != 0)[0][0])
+    bad[k, n] = 0  # a missing link without a rule
+    with pytest.raises(lbm_mod.LBMError) as e:
+        lbm_mod.LBMSolid(geo.nx, geo.nx, geo.dx, 0.1, 0.7, periodic=False,
+                         node_mask=geo.active, link_bc=bad, wall_d=wd, wall_T=wT,
+                         wall_n=geo.normal)
+    assert e.value.status == lbm_mod.LBM_ERR_ARG
