@@ -165,6 +165,40 @@ lbm_status lbm_solid_displacement(lbm_solid *h, double *d_dev);
 /* Number of kernel launches this handle has issued (for launch accounting). */
 long lbm_solid_launch_count(const lbm_solid *h);
 
+/* Objective without any device allocation.
+ *
+ * The paper has no counterpart to this entry point: it exists for callers that cannot
+ * allocate device memory, and so cannot create a handle (lbm_solid_create allocates).
+ * Examples: a host application that gives all device memory to its own pool and
+ * forbids other allocations, or a loop that must not pay the device-wide
+ * synchronisation that cudaFree implies.  It computes the same J as
+ * lbm_solid_objective (Eqs. node_J, discrete_J) from caller-owned device arrays and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   fS_dev    8N post-streaming populations, SoA [k*N + n] (e.g. from
+ *             lbm_solid_get_populations(h, 0, ...))
+ *   F_dev     2N physical body force (d = m10 + dx^2 F / 2, Eq. moments_bar_1/2)
+ *   dstar_dev 2N target displacement;  obs_dev  N weights of Omega^J, or NULL = all 1
+ *   J_dev     1 double, written with J = (1/2) sum obs |d - d*|^2 / sum obs |d*|^2
+ *             (the dx^2 factors of J and Cbar cancel); NaN if the target has zero norm
+ *   stream    cudaStream_t the two kernels are enqueued on (NULL = legacy stream);
+ *             the call returns without synchronising.
+ *
+ * Scratch: per-block partial sums live in one fixed file-scope __device__ array of
+ * 2 * LBM_NOALLOC_MAX_NODES / 256 doubles (64 KiB), which every GPU that loads this
+ * library holds until the process exits.  Grids with nx * ny > LBM_NOALLOC_MAX_NODES
+ * are rejected with LBM_ERR_ARG before anything is launched.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  All calls on a device
+ * share the array and every call rewrites the partials it reads, but calls that
+ * overlap on the GPU (other streams, other host threads) race on it: serialise them.
+ * Returns LBM_ERR_ARG for invalid sizes or NULL arrays, LBM_ERR_CUDA if the address
+ * lookup or a launch fails. */
+#define LBM_NOALLOC_MAX_NODES (1L << 20)
+lbm_status lbm_objective_noalloc(int nx, int ny, double dx, const double *fS_dev,
+                                 const double *F_dev, const double *dstar_dev,
+                                 const double *obs_dev, double *J_dev, void *stream);
+
 const char *lbm_status_string(lbm_status s);
 const char *lbm_solid_last_error(const lbm_solid *h);
 

@@ -29,7 +29,7 @@ EXPORTED = [
     "lbm_solid_primal_solve", "lbm_solid_objective", "lbm_solid_adjoint_solve",
     "lbm_solid_gradient", "lbm_solid_get_populations", "lbm_solid_set_populations",
     "lbm_solid_displacement", "lbm_solid_launch_count", "lbm_status_string",
-    "lbm_solid_last_error",
+    "lbm_solid_last_error", "lbm_objective_noalloc",
 ]
 
 
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_solid_launch_count": ([P], ctypes.c_long),
         "lbm_status_string": ([I], ctypes.c_char_p),
         "lbm_solid_last_error": ([P], ctypes.c_char_p),
+        "lbm_objective_noalloc": ([I, I, D, P, P, P, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
