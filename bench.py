@@ -101,23 +101,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def csrc_digest():
+    """sha256 over the CUDA sources (sorted file names), to tie a stored ncu figure to the
+    exact kernel code it was taken on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2609_31347_b300", "csrc")
+    h = hashlib.sha256()
+    for p in sorted(os.listdir(d)):
+        with open(os.path.join(d, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def traffic_from_profiles(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
-    on the current kernel source (hash match); otherwise None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per 4096^2 launch of `kernel` from profiles/traffic.txt (lines
+    'kernel bytes_per_launch csrc_sha256'), if taken on the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
+        digest = csrc_digest()
         with open(path) as fh:
-            t = json.load(fh)
-        from paper_2609_31347_b300 import build as b
-        import hashlib
-        h = hashlib.sha256()
-        for p in sorted(os.listdir(os.path.join(ROOT, "paper_2609_31347_b300", "csrc"))):
-            with open(os.path.join(ROOT, "paper_2609_31347_b300", "csrc", p), "rb") as fh:
-                h.update(fh.read())
-        ent = t.get(kernel)
-        if ent and ent.get("csrc_sha256") == h.hexdigest():
-            return ent["bytes_per_launch"]
-    except Exception:
+            for line in fh:
+                parts = line.split("#", 1)[0].split()
+                if len(parts) == 3 and parts[0] == kernel and parts[2] == digest:
+                    return float(parts[1])
+    except OSError:
         pass
     return None
 
@@ -195,6 +202,8 @@ def main():
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--sweeps", type=int, default=100, help="primal (and adjoint) sweeps per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "fp64"],
+                    help="sweep arithmetic: integer-pipe fixed point (auto) or FP64 pipe")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -220,7 +229,8 @@ def main():
     F_dev = torch.as_tensor(F.ravel(), device="cuda")
     d_dev = torch.as_tensor(dstar.ravel(), device="cuda")
     g_dev = torch.empty(2 * N, dtype=torch.float64, device="cuda")
-    s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu, periodic=True, control="force_field")
+    s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu, periodic=True, control="force_field",
+                     kernel=args.kernel)
     s.set_target(d_dev)
     stream = torch.cuda.current_stream()
 
@@ -287,8 +297,21 @@ def main():
     sweep_s = primal_ms * 1e-3
     achieved_gbs = BYTES_PER_LUP * N / sweep_s / 1e9
     dp_peak = FP64_LANES_PER_SM * NUM_SMS * sm_mhz * 1e6 / 1e9  # G FP64 instructions / s
-    dp_achieved = FP64_OPS_PER_LUP * N / sweep_s / 1e9
-    traffic = traffic_from_profiles("k_primal")
+    kname = "k_primal<periodic, %s>" % ("FP64 pipe" if args.kernel == "fp64" else "fixed point")
+    traffic = traffic_from_profiles("k_primal_" + args.kernel)
+    if args.kernel == "fp64":
+        dp_achieved = FP64_OPS_PER_LUP * N / sweep_s / 1e9
+        roof = {"bound": "alu", "achieved": dp_achieved, "peak": dp_peak, "unit": "G FP64 inst/s",
+                "frac": dp_achieved / dp_peak, "traffic": traffic, "kernel": kname,
+                "peak_kind": "derived: 2 FP64 lanes/SM x 148 SMs x %.0f MHz" % sm_mhz,
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                        "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_gbs, "traffic": traffic, "kernel": kname,
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_lup": BYTES_PER_LUP,
+                "units_per_launch": N}
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -296,20 +319,30 @@ def main():
         "data": "synthetic (8-mode Fourier force, seed 1; random target)",
         "config": {"workload": WORKLOAD, "nx": nx, "ny": nx, "sweeps_per_step": K,
                    "E": E, "nu": nu, "l2_flush": "not needed: each lattice is 1.07 GB > L2",
-                   "kernel": "fp64"},
-        "roofline": {"bound": "alu", "achieved": dp_achieved, "peak": dp_peak,
-                     "unit": "G FP64 inst/s", "frac": dp_achieved / dp_peak,
-                     "traffic": traffic, "kernel": "k_primal (primal sweep)",
-                     "peak_kind": "derived: 2 FP64 lanes/SM x 148 SMs x %.0f MHz" % sm_mhz,
-                     "hbm": {"achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
-                             "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind,
-                             "algorithmic_bytes_per_lup": BYTES_PER_LUP}},
+                   "kernel": args.kernel},
+        "roofline": roof,
         "sweep_ms": {"primal": primal_ms, "adjoint": adjoint_ms},
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 16 * N,
                 "d2h_bytes_per_step": 16 * N + 8},
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if args.kernel != "fp64" and rank == 0:
+        # the strict FP64-pipe variant on the same workload, for comparison
+        s.close()
+        s2 = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu, periodic=True, control="force_field",
+                          kernel="fp64")
+        s2.set_target(d_dev)
+        s2.set_control(F_dev)
+        s2.primal_solve(5, fixed_steps=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s2.primal_solve(20, fixed_steps=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t2 = e0.elapsed_time(e1) / 20
+        out["fp64_pipe_variant"] = {"primal_sweep_ms": t2, "primal_glups": N / (t2 * 1e-3) / 1e9}
+        s = s2
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:

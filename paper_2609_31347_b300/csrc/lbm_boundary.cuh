@@ -95,14 +95,42 @@ __device__ inline T boundary_rule(const BoundaryNode &bn, int k, const T (&fc)[8
   return -fc[kb] + p2[k];
 }
 
+// Material and its E-derivatives from a modulus (per-node field control).
+__device__ inline Material material_of(double E, double nu) {
+  const double mu = E / (2.0 * (1.0 + nu)), K = E / (2.0 * (1.0 - nu));
+  const double t11 = mu / kTheta, ts = 2.0 * K / (1.0 + kTheta), td = 2.0 * mu / (1.0 - kTheta);
+  const double dmu = 1.0 / (2.0 * (1.0 + nu)), dK = 1.0 / (2.0 * (1.0 - nu));
+  Material m;
+  m.w11 = 1.0 / (t11 + 0.5);
+  m.ws = 1.0 / (ts + 0.5);
+  m.wd = 1.0 / (td + 0.5);
+  m.K = K;
+  m.dw11 = -m.w11 * m.w11 * dmu / kTheta;
+  m.dws = -m.ws * m.ws * 2.0 * dK / (1.0 + kTheta);
+  m.dwd = -m.wd * m.wd * 2.0 * dmu / (1.0 - kTheta);
+  m.dK = dK;
+  return m;
+}
+
 // One thread per boundary record: Q (row-major [k*8+j]) and s, and their derivatives
-// with respect to E (dQ, ds; skipped when dQ == nullptr).
-__global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, long nb, Material m,
+// with respect to E (dQ, ds; skipped when dQ == nullptr).  With a modulus field
+// (alpha != nullptr) each record takes the material of its own node and also stores
+// its boundary gamma (Eq. gamma with tau_f = 1/2).
+__global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, long nb, Material m0,
                                  double dx, double *__restrict__ Q, double *__restrict__ s,
-                                 double *__restrict__ dQ, double *__restrict__ ds) {
+                                 double *__restrict__ dQ, double *__restrict__ ds,
+                                 const double *__restrict__ alpha, const int *__restrict__ bnode,
+                                 double nu, double *__restrict__ gam) {
   const long b = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const BoundaryNode bn = nodes[b];
+  Material m = m0;
+  if (alpha) {
+    const double a = alpha[bnode[b]];
+    m = material_of(a * a, nu);
+    const double ts = 1.0 / m.ws - 0.5;
+    gam[b] = kTheta * 0.5 / ((1.0 + kTheta) * (ts - 0.5));
+  }
   const Dual w[3] = {Dual(m.w11, m.dw11), Dual(m.ws, m.dws), Dual(m.wd, m.dwd)};
   const Dual K(m.K, m.dK);
   for (int k = 0; k < 8; ++k) {

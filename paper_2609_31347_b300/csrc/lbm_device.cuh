@@ -24,6 +24,16 @@ namespace lbm {
 
 constexpr double kTheta = 1.0 / 3.0;
 
+// Fixed-point constant C = round(c 2^62) = hi 2^31 + lo, 0 <= lo < 2^31, |c| < 1/2
+// (used by the integer-pipe variant in lbm_fixed.cuh).
+struct FixC {
+  int hi, lo;
+};
+
+struct CoefFix {
+  FixC qs, qd, q11, third;  // cs/4, cd/4, c11/4, 1/3
+};
+
 // Per-material constants (host-computed, passed by value).
 struct Coef {
   double c11, cs, cd;  // 1 - omega for m11, m_s, m_d
@@ -34,7 +44,38 @@ struct Coef {
   // pre-scaled factors of the pair-form inverse (bulk and boundary rows)
   double q11, qs, qd;  // c11 / 4, cs / 4, cd / 4
   double qs_b, P_b;    // boundary: cs (1/4 + gamma/2) and -gamma cs / 4
+  CoefFix fx;          // the bulk constants in fixed point
 };
+
+// Per-node material of the Young's-modulus field control: q planes hold c/4 for
+// (m11, m_s, m_d) per node, gam the boundary gamma per boundary record.
+struct Field {
+  const double *q;      // 3N: c11/4, cs/4, cd/4
+  const double *gam;    // nb
+  const double *alpha;  // N: control, E_n = alpha_n^2
+  double nu;
+};
+
+// The node's collision constants: the handle's for a uniform material, or the per-node
+// planes of a modulus field (boundary rows from the record's gamma).
+template <bool FIELD>
+__device__ __forceinline__ Coef node_coef(const Coef &c, const Field &fl, long N, long n,
+                                          int bi) {
+  if (!FIELD) return c;
+  Coef r = c;
+  r.q11 = fl.q[n];
+  r.qs = fl.q[N + n];
+  r.qd = fl.q[2 * N + n];
+  r.c11 = 4.0 * r.q11;
+  r.cs = 4.0 * r.qs;
+  r.cd = 4.0 * r.qd;
+  if (bi >= 0) {
+    r.gam = fl.gam[bi];
+    r.qs_b = r.cs * (0.25 + 0.5 * r.gam);
+    r.P_b = -0.25 * r.gam * r.cs;
+  }
+  return r;
+}
 
 constexpr double kHalfOneMinusTheta = 0.5 * (1.0 - kTheta);
 constexpr double kQuarterTheta = 0.25 * kTheta;

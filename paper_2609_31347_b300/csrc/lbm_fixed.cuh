@@ -1,0 +1,164 @@
+// Integer-pipe variant of the collision and transposed collision (sm_103a).
+//
+// B300 executes FP64 at 2 lanes per SM (measured 1.86 DFMA/clk/SM) but 32-bit integer
+// add/logic at ~128 lanes and 32x32->64 multiply-add at ~64 lanes per SM.  The sweep
+// does ~37 FP64 operations per node, so on the FP64 pipe it is ALU-bound at ~1/3 of the
+// HBM roofline.  This variant keeps every population in HBM as IEEE binary64 and does
+// the node's arithmetic in 64-bit fixed point on the integer pipes:
+//
+//   unpack  all ten inputs of a node (8 populations + 2 force or adjoint-source values)
+//           share the node's largest exponent E: x -> v = trunc(x 2^(1079-E)) by moving
+//           the exponent field and one cvt.rzi.s64.f64, so |v| < 2^57 (the largest
+//           input has 56-57 significant bits; smaller ones keep all bits down to
+//           2^-57 of the node maximum);
+//   compute the same pair-form maps as lbm_device.cuh with int64 adds, arithmetic
+//           shifts for the powers of two, and a truncated 64x62-bit fixed-point
+//           multiply (three mul.wide.s32) for the five non-power-of-two constants;
+//           intermediates stay below 2^61;
+//   pack    v -> |v| 2^(E-1079) rounded to nearest binary64 (clz, shift, exponent
+//           assembly, round bit added with carry into the exponent field).
+//
+// Every result is within a few units of 2^-56 of the node's largest input of the exact
+// value (binary64 rounding of the FP64-pipe variant is 2^-53 of each operand), far
+// inside the 1e-11 parity bound.  Nodes whose largest exponent exceeds 2000 (values
+// near overflow, Inf, NaN) take the FP64-pipe path so that Inf/NaN propagate.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// (v c) with v < 2^61 in magnitude: v = vh 2^31 + vl, v C = vh hi 2^62 +
+// (vh lo + vl hi) 2^31 + vl lo; the last term (< 2^62, i.e. < 1 unit after >> 62) is
+// dropped.
+__device__ __forceinline__ long long mulfix(long long v, FixC c) {
+  const int vh = (int)(v >> 31);
+  const int vl = (int)(v & 0x7fffffffll);
+  long long t = (long long)vh * c.lo;
+  t += (long long)vl * c.hi;
+  return (long long)vh * c.hi + (t >> 31);
+}
+
+__device__ __forceinline__ int exp_of(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+// x 2^sh truncated toward zero (0 for zero / subnormal inputs or results below the
+// smallest normal number).
+__device__ __forceinline__ long long to_fix(double x, int ex, int sh) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const bool keep = (ex != 0) && (ex + sh > 0);
+  const double y = __hiloint2double(keep ? hi + (int)((unsigned)sh << 20) : 0, keep ? lo : 0);
+  return __double2ll_rz(y);
+}
+
+// v 2^(E-1079) rounded to nearest (ties away from zero); tiny results flush to 0.
+__device__ __forceinline__ double from_fix(long long v, int E) {
+  const unsigned long long s = (unsigned long long)(v >> 63);
+  const unsigned long long a = ((unsigned long long)v ^ s) - s;
+  const int lz = __clzll((long long)a);
+  const int ef = E + 7 - lz;
+  const unsigned long long m = a << (lz & 63);
+  unsigned long long bits =
+      ((unsigned long long)(unsigned)(ef - 1) << 52) + (m >> 11) + ((m >> 10) & 1ull);
+  bits |= s & 0x8000000000000000ull;
+  if (a == 0 || ef <= 0) bits = 0;
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ int max_exp10(const double (&f)[8], double a, double b, int (&e)[10]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) e[k] = exp_of(f[k]);
+  e[8] = exp_of(a);
+  e[9] = exp_of(b);
+  int E = e[0];
+#pragma unroll
+  for (int k = 1; k < 10; ++k) E = max(E, e[k]);
+  return E;
+}
+
+// Bulk collision in fixed point (same map as collide<false>).  Returns false when the
+// node must take the FP64-pipe path (largest exponent > 2000).
+template <bool MON>
+__device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, double qy,
+                                            const CoefFix &c, double (&o)[8], double &dx_,
+                                            double &dy_) {
+  int e[10];
+  const int E = max_exp10(f, qx, qy, e);
+  if (E > 2000) return false;
+  const int sh = 1079 - E;
+  long long F[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) F[k] = to_fix(f[k], e[k], sh);
+  const long long QX = to_fix(qx, e[8], sh), QY = to_fix(qy, e[9], sh);
+  const long long a1 = F[0] + F[2], b1 = F[0] - F[2];
+  const long long a2 = F[1] + F[3], b2 = F[1] - F[3];
+  const long long a3 = F[4] + F[6], b3 = F[4] - F[6];
+  const long long a4 = F[5] + F[7], b4 = F[5] - F[7];
+  const long long mb10 = b1 + (b3 - b4) + 2 * QX;
+  const long long mb01 = b2 + (b3 + b4) + 2 * QY;
+  const long long m11 = a3 - a4;
+  const long long ms = a1 + a2 + 2 * (a3 + a4);
+  const long long md = a1 - a2;
+  const long long es = mulfix(ms, c.qs);
+  const long long td = mulfix(md, c.qd);
+  const long long e1 = es + td, e2 = es - td;
+  const long long t10 = mulfix(mb10, c.third), t01 = mulfix(mb01, c.third);
+  const long long o1 = t10 + QX, o2 = t01 + QY;
+  const long long u = (t10 + t01) >> 2, v = (t01 - t10) >> 2;
+  const long long q11 = mulfix(m11, c.q11);
+  o[0] = from_fix(e1 + o1, E);
+  o[2] = from_fix(e1 - o1, E);
+  o[1] = from_fix(e2 + o2, E);
+  o[3] = from_fix(e2 - o2, E);
+  o[4] = from_fix(q11 + u, E);
+  o[6] = from_fix(q11 - u, E);
+  o[5] = from_fix(v - q11, E);
+  o[7] = from_fix(-q11 - v, E);
+  if (MON) {
+    dx_ = from_fix(mb10, E);
+    dy_ = from_fix(mb01, E);
+  }
+  return true;
+}
+
+// Bulk transposed collision in fixed point (same map as collide_T<false>).
+template <bool MON>
+__device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, double ry,
+                                              const CoefFix &c, double (&o)[8], double &ax,
+                                              double &ay) {
+  int e[10];
+  const int E = max_exp10(p, rx, ry, e);
+  if (E > 2000) return false;
+  const int sh = 1079 - E;
+  long long P[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) P[k] = to_fix(p[k], e[k], sh);
+  const long long RX = to_fix(rx, e[8], sh), RY = to_fix(ry, e[9], sh);
+  const long long A1 = P[0] + P[2], B1 = P[0] - P[2];
+  const long long A2 = P[1] + P[3], B2 = P[1] - P[3];
+  const long long A3 = P[4] + P[6], B3 = P[4] - P[6];
+  const long long A4 = P[5] + P[7], B4 = P[5] - P[7];
+  const long long d34 = B3 - B4, s34 = B3 + B4;
+  // (1/3) B1 + (1/12) d34 - rx = (1/3) (B1 + d34/4) - rx
+  const long long n10 = mulfix(B1 + (d34 >> 2), c.third) - RX;
+  const long long n01 = mulfix(B2 + (s34 >> 2), c.third) - RY;
+  const long long n11 = mulfix(A3 - A4, c.q11);
+  const long long ns = mulfix(A1 + A2, c.qs);
+  const long long nd = mulfix(A1 - A2, c.qd);
+  const long long S1 = ns + nd, S2 = ns - nd;
+  o[0] = from_fix(S1 + n10, E);
+  o[2] = from_fix(S1 - n10, E);
+  o[1] = from_fix(S2 + n01, E);
+  o[3] = from_fix(S2 - n01, E);
+  const long long T1 = 2 * ns + n11, T2 = 2 * ns - n11;
+  const long long P1 = n10 + n01, P2 = n01 - n10;
+  o[4] = from_fix(T1 + P1, E);
+  o[6] = from_fix(T1 - P1, E);
+  o[5] = from_fix(T2 + P2, E);
+  o[7] = from_fix(T2 - P2, E);
+  if (MON) {
+    ax = from_fix(B1 + d34, E);
+    ay = from_fix(B2 + s34, E);
+  }
+  return true;
+}
+
+}  // namespace lbm

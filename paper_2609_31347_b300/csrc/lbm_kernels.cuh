@@ -12,6 +12,7 @@
 // wall stress for Neumann), and a bit mask of the regular links.
 #pragma once
 #include "lbm_device.cuh"
+#include "lbm_fixed.cuh"
 
 namespace lbm {
 
@@ -154,11 +155,14 @@ __device__ __forceinline__ bool pull_adjoint(const double *__restrict__ pin, int
 }
 
 // One primal sweep: f_C(t) = C[S' f_C(t-1), g]; optional monitor partial sum of |d|^2.
-template <bool BOUNDED, bool MONITOR>
+// ARITH 0: every operation on the FP64 pipe; ARITH 1: bulk nodes in 64-bit fixed point
+// on the integer pipes (lbm_fixed.cuh), boundary nodes on the FP64 pipe.
+template <bool BOUNDED, bool MONITOR, int ARITH, bool FIELD>
 __global__ void __launch_bounds__(256) k_primal(const double *__restrict__ fin,
                                                 double *__restrict__ fout,
                                                 const double *__restrict__ g2, Grid g,
-                                                Bounded b, Coef c, double *__restrict__ partial) {
+                                                Bounded b, Coef c0, Field fl,
+                                                double *__restrict__ partial) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   double mon[1] = {0.0};
@@ -166,11 +170,13 @@ __global__ void __launch_bounds__(256) k_primal(const double *__restrict__ fin,
     const long n = (long)y * g.nx + x;
     double f[8], gsel;
     if (pull_primal<BOUNDED>(fin, x, y, g, b, f, gsel)) {
-      double o[8], dxn, dyn;
+      double o[8], dxn = 0.0, dyn = 0.0;
       const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+      const Coef c = node_coef<FIELD>(c0, fl, g.N, n,
+                                      (BOUNDED && FIELD && gsel != 0.0) ? b.bidx[n] : -1);
       if (BOUNDED && gsel != 0.0)
         collide<true>(f, qx, qy, c, o, dxn, dyn);
-      else
+      else if (ARITH == 0 || !collide_fix<MONITOR>(f, qx, qy, c.fx, o, dxn, dyn))
         collide<false>(f, qx, qy, c, o, dxn, dyn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
@@ -184,29 +190,33 @@ __global__ void __launch_bounds__(256) k_primal(const double *__restrict__ fin,
   }
 }
 
-// Collision only (first sweep from an explicit f_S state): fout = C[fin, g].
-template <bool BOUNDED>
+// Collision only (first sweep from an explicit f_S state): fout = C[fin, g], with the
+// same arithmetic as k_primal so that a restart from a checkpoint reproduces the
+// uninterrupted run bit for bit.
+template <bool BOUNDED, int ARITH, bool FIELD>
 __global__ void __launch_bounds__(256) k_collide_only(const double *__restrict__ fin,
                                                       double *__restrict__ fout,
                                                       const double *__restrict__ g2, Grid g,
-                                                      Bounded b, Coef c) {
+                                                      Bounded b, Coef c0, Field fl) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
   const long n = (long)y * g.nx + x;
-  double gsel = 0.0;
+  bool bnd = false;
   if (BOUNDED) {
     const uint8_t t = b.type[n];
     if (t == 0) return;
-    gsel = t == 2 ? 1.0 : 0.0;
+    bnd = t == 2;
   }
+  const Coef c = node_coef<FIELD>(c0, fl, g.N, n, (FIELD && bnd) ? b.bidx[n] : -1);
   double f[8], o[8], dxn, dyn;
 #pragma unroll
   for (int k = 0; k < 8; ++k) f[k] = fin[k * g.N + n];
-  if (gsel != 0.0)
-    collide<true>(f, g2[n], g2[g.N + n], c, o, dxn, dyn);
-  else
-    collide<false>(f, g2[n], g2[g.N + n], c, o, dxn, dyn);
+  const double qx = g2[n], qy = g2[g.N + n];
+  if (bnd)
+    collide<true>(f, qx, qy, c, o, dxn, dyn);
+  else if (ARITH == 0 || !collide_fix<false>(f, qx, qy, c.fx, o, dxn, dyn))
+    collide<false>(f, qx, qy, c, o, dxn, dyn);
 #pragma unroll
   for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
 }
@@ -310,11 +320,12 @@ __global__ void __launch_bounds__(256) k_objective(const double *__restrict__ sr
 }
 
 // One adjoint sweep: phi_C(k+1) = A^T S'^T phi_C(k) - j; optional monitor of |d^phi|^2.
-template <bool BOUNDED, bool MONITOR>
+template <bool BOUNDED, bool MONITOR, int ARITH, bool FIELD>
 __global__ void __launch_bounds__(256) k_adjoint(const double *__restrict__ pin,
                                                  double *__restrict__ pout,
                                                  const double *__restrict__ r, Grid g,
-                                                 Bounded b, Coef c, double *__restrict__ partial) {
+                                                 Bounded b, Coef c0, Field fl,
+                                                 double *__restrict__ partial) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   double mon[1] = {0.0};
@@ -322,11 +333,14 @@ __global__ void __launch_bounds__(256) k_adjoint(const double *__restrict__ pin,
     const long n = (long)y * g.nx + x;
     double p[8], gsel;
     if (pull_adjoint<BOUNDED>(pin, x, y, g, b, p, gsel)) {
-      double o[8], ax, ay;
+      double o[8], ax = 0.0, ay = 0.0;
+      const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
+      const Coef c = node_coef<FIELD>(c0, fl, g.N, n,
+                                      (BOUNDED && FIELD && gsel != 0.0) ? b.bidx[n] : -1);
       if (BOUNDED && gsel != 0.0)
-        collide_T<true>(p, __ldg(r + n), __ldg(r + g.N + n), c, o, ax, ay);
-      else
-        collide_T<false>(p, __ldg(r + n), __ldg(r + g.N + n), c, o, ax, ay);
+        collide_T<true>(p, rx, ry, c, o, ax, ay);
+      else if (ARITH == 0 || !collide_T_fix<MONITOR>(p, rx, ry, c.fx, o, ax, ay))
+        collide_T<false>(p, rx, ry, c, o, ax, ay);
 #pragma unroll
       for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
       if (MONITOR) mon[0] = ax * ax + ay * ay;
@@ -387,10 +401,11 @@ __global__ void __launch_bounds__(256) k_grad_force(const double *__restrict__ p
 // c11 scales m11/4 on the diagonals (+,-,+,-), cs scales m_s on the axis pairs
 // (1/4 + gamma/2) and on the diagonals (-gamma/4), cd scales m_d/4 on the axis pairs
 // (+,-,+,-), gamma scales cs m_s (1/2 on axis, -1/4 on diagonals).
-template <bool BOUNDED>
+template <bool BOUNDED, bool FIELD>
 __global__ void __launch_bounds__(256) k_grad_young(const double *__restrict__ fin,
                                                     const double *__restrict__ pin, Grid g,
-                                                    Bounded b, Coef c, YoungDeriv yd,
+                                                    Bounded b, Coef c0, YoungDeriv yd0, Field fl,
+                                                    double *__restrict__ grad,
                                                     double *__restrict__ partial) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -398,20 +413,35 @@ __global__ void __launch_bounds__(256) k_grad_young(const double *__restrict__ f
   if (x < g.nx && y < g.ny) {
     const long n = (long)y * g.nx + x;
     double f[8], p[8], gsel, gsel2;
+    double gn = 0.0;
     if (pull_primal<BOUNDED>(fin, x, y, g, b, f, gsel) &&
         pull_adjoint<BOUNDED>(pin, x, y, g, b, p, gsel2)) {
+      const bool bnd = BOUNDED && gsel != 0.0;
+      const int bi = bnd ? b.bidx[n] : -1;
+      const Coef c = node_coef<FIELD>(c0, fl, g.N, n, bi);
+      YoungDeriv yd = yd0;
+      if (FIELD) {
+        // d(1 - omega)/dE = omega^2 dtau/dE with the node's omega = 1 - c
+        const double w11 = 1.0 - c.c11, ws = 1.0 - c.cs, wd = 1.0 - c.cd;
+        const double dt11 = 1.0 / (2.0 * (1.0 + fl.nu) * kTheta);
+        const double dts = 1.0 / ((1.0 - fl.nu) * (1.0 + kTheta));
+        const double dtd = 1.0 / ((1.0 + fl.nu) * (1.0 - kTheta));
+        yd.dc11 = w11 * w11 * dt11;
+        yd.dcs = ws * ws * dts;
+        yd.dcd = wd * wd * dtd;
+        const double ts = 1.0 / ws - 0.5;
+        yd.dgam = BOUNDED ? -kTheta * 0.5 * dts / ((1.0 + kTheta) * (ts - 0.5) * (ts - 0.5)) : 0.0;
+      }
       const double m11 = (f[4] + f[6]) - (f[5] + f[7]);
       const double ms = (f[0] + f[1] + f[2] + f[3]) + 2.0 * (f[4] + f[5] + f[6] + f[7]);
       const double md = (f[0] + f[2]) - (f[1] + f[3]);
       const double pax = p[0] + p[1] + p[2] + p[3], pdg = p[4] + p[5] + p[6] + p[7];
-      const bool bnd = BOUNDED && gsel != 0.0;
       const double gam = bnd ? c.gam : 0.0;
       double t = yd.dc11 * 0.25 * m11 * ((p[4] + p[6]) - (p[5] + p[7]));
       t += yd.dcd * 0.25 * md * ((p[0] + p[2]) - (p[1] + p[3]));
       t += yd.dcs * ms * ((0.25 + 0.5 * gam) * pax - 0.25 * gam * pdg);
       if (bnd) {
         t += yd.dgam * c.cs * ms * (0.5 * pax - 0.25 * pdg);
-        const int bi = b.bidx[n];
         const unsigned reg = b.regmask[bi];
         double own[8];
 #pragma unroll
@@ -424,12 +454,35 @@ __global__ void __launch_bounds__(256) k_grad_young(const double *__restrict__ f
           t += __ldg(pin + k * g.N + n) * ds_;
         }
       }
-      acc[0] = -t;
+      gn = -t;
     }
+    if (FIELD)
+      grad[n] = 2.0 * fl.alpha[n] * gn;  // E_n = alpha_n^2
+    else
+      acc[0] = gn;
   }
-  __shared__ double sm[32];
-  block_sum<1>(acc, sm);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
+  if (!FIELD) {
+    __shared__ double sm[32];
+    block_sum<1>(acc, sm);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
+  }
+}
+
+// Per-node collision constants of a modulus field: E_n = alpha_n^2 (Eq. E_substitution),
+// plane-stress moduli (Eqs. mu, K), relaxation (Table A.1, Eq. relaxation).
+__global__ void k_set_young_field(const double *__restrict__ alpha, double nu, long N,
+                                  double *__restrict__ q) {
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N;
+       n += (long)gridDim.x * blockDim.x) {
+    const double E = alpha[n] * alpha[n];
+    const double mu = E / (2.0 * (1.0 + nu)), K = E / (2.0 * (1.0 - nu));
+    const double w11 = 1.0 / (mu / kTheta + 0.5);
+    const double ws = 1.0 / (2.0 * K / (1.0 + kTheta) + 0.5);
+    const double wd = 1.0 / (2.0 * mu / (1.0 - kTheta) + 0.5);
+    q[n] = 0.25 * (1.0 - w11);
+    q[N + n] = 0.25 * (1.0 - ws);
+    q[2 * N + n] = 0.25 * (1.0 - wd);
+  }
 }
 
 // Subtract per-component means over active nodes (Eq. zero_mean_projection).

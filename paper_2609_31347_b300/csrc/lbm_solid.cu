@@ -40,6 +40,11 @@ struct lbm_solid {
   double *Q = nullptr, *s = nullptr, *dQ = nullptr, *ds = nullptr;
   YoungDeriv yd{};
   double alpha = 0.0;  // scalar Young control (E = alpha^2)
+  // modulus field control: per-node constants, control copy, per-record gamma / node
+  double *qfield = nullptr, *alphaN = nullptr, *gamf = nullptr;
+  int *bnode = nullptr;
+  Field fl{};
+  bool field = false;
   BoundaryNode *bnodes = nullptr;
   long nb = 0;
   double *partial = nullptr;
@@ -86,6 +91,13 @@ lbm_status fail(lbm_solid *h, lbm_status st, const std::string &msg) {
 
 constexpr double kTh = 1.0 / 3.0;
 
+// c -> round(c 2^62) split as hi 2^31 + lo with 0 <= lo < 2^31 (|c| < 1/2).
+FixC to_fixc(double c) {
+  const long long C = std::llround(std::ldexp(c, 62));
+  const long long hi = C >> 31;  // arithmetic shift: floor
+  return FixC{(int)hi, (int)(C - hi * (1LL << 31))};
+}
+
 // Material map (Eqs. lambda, mu, K) and relaxation (Table A.1, Eq. relaxation, Eq. gamma).
 bool material_coefs(double E, double nu, bool bounded, bool neumann, Coef &c, Material &m,
                     YoungDeriv &yd, std::string &why) {
@@ -107,6 +119,7 @@ bool material_coefs(double E, double nu, bool bounded, bool neumann, Coef &c, Ma
     }
   }
   c.q11 = 0.25 * c.c11; c.qs = 0.25 * c.cs; c.qd = 0.25 * c.cd;
+  c.fx = CoefFix{to_fixc(c.qs), to_fixc(c.qd), to_fixc(c.q11), to_fixc(1.0 / 3.0)};
   c.qs_b = c.cs * (0.25 + 0.5 * c.gam);
   c.P_b = -0.25 * c.gam * c.cs;
   // derivatives with respect to E: d omega = -omega^2 d tau
@@ -123,8 +136,9 @@ lbm_status setup_boundary(lbm_solid *h) {
   if (h->periodic || h->nb == 0) return LBM_OK;
   const unsigned threads = 128;
   const unsigned blocks = (unsigned)((h->nb + threads - 1) / threads);
-  k_boundary_setup<<<blocks, threads, 0, h->stream>>>(h->bnodes, h->nb, h->mat, h->dx, h->Q, h->s,
-                                                      h->dQ, h->ds);
+  k_boundary_setup<<<blocks, threads, 0, h->stream>>>(
+      h->bnodes, h->nb, h->mat, h->dx, h->Q, h->s, h->dQ, h->ds, h->field ? h->alphaN : nullptr,
+      h->bnode, h->nu, h->gamf);
   LAUNCHED(h);
   return LBM_OK;
 }
@@ -156,23 +170,61 @@ lbm_status fetch(lbm_solid *h, int nv) {
   return LBM_OK;
 }
 
-// One primal sweep; optional monitor partials (nblocks2d sums of |d|^2).
-lbm_status primal_sweep(lbm_solid *h, bool monitor) {
-  if (h->fcur_is_fs) {
-    if (h->periodic)
-      k_collide_only<false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef);
-    else
-      k_collide_only<true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef);
-  } else if (h->periodic) {
+template <int A, bool F>
+void launch_primal(lbm_solid *h, bool monitor) {
+  if (h->periodic) {
     if (monitor)
-      k_primal<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->partial);
+      k_primal<false, true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl, h->partial);
     else
-      k_primal<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, nullptr);
+      k_primal<false, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl, nullptr);
   } else {
     if (monitor)
-      k_primal<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->partial);
+      k_primal<true, true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl, h->partial);
     else
-      k_primal<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, nullptr);
+      k_primal<true, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl, nullptr);
+  }
+}
+
+template <int A, bool F>
+void launch_adjoint(lbm_solid *h, bool monitor) {
+  if (h->periodic) {
+    if (monitor)
+      k_adjoint<false, true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->fl, h->partial);
+    else
+      k_adjoint<false, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->fl, nullptr);
+  } else {
+    if (monitor)
+      k_adjoint<true, true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->fl, h->partial);
+    else
+      k_adjoint<true, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->fl, nullptr);
+  }
+}
+
+template <int A, bool F>
+void launch_collide_only(lbm_solid *h) {
+  if (h->periodic)
+    k_collide_only<false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl);
+  else
+    k_collide_only<true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl);
+}
+
+// One primal sweep; optional monitor partials (nblocks2d sums of |d|^2).  Arithmetic:
+// FP64 pipe for LBM_KERNEL_FP64 and for modulus fields, fixed point otherwise.
+lbm_status primal_sweep(lbm_solid *h, bool monitor) {
+  const bool fp = h->kernel == LBM_KERNEL_FP64;
+  if (h->fcur_is_fs) {
+    if (h->field)
+      launch_collide_only<0, true>(h);
+    else if (fp)
+      launch_collide_only<0, false>(h);
+    else
+      launch_collide_only<1, false>(h);
+  } else if (h->field) {
+    launch_primal<0, true>(h, monitor);
+  } else if (fp) {
+    launch_primal<0, false>(h, monitor);
+  } else {
+    launch_primal<1, false>(h, monitor);
   }
   LAUNCHED(h);
   std::swap(h->fcur, h->fnext);
@@ -181,20 +233,21 @@ lbm_status primal_sweep(lbm_solid *h, bool monitor) {
 }
 
 lbm_status adjoint_sweep(lbm_solid *h, bool monitor) {
-  if (h->periodic) {
-    if (monitor)
-      k_adjoint<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->partial);
-    else
-      k_adjoint<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, nullptr);
-  } else {
-    if (monitor)
-      k_adjoint<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->partial);
-    else
-      k_adjoint<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, nullptr);
-  }
+  if (h->field)
+    launch_adjoint<0, true>(h, monitor);
+  else if (h->kernel == LBM_KERNEL_FP64)
+    launch_adjoint<0, false>(h, monitor);
+  else
+    launch_adjoint<1, false>(h, monitor);
   LAUNCHED(h);
   std::swap(h->pcur, h->pnext);
   return LBM_OK;
+}
+
+lbm_status set_field(lbm_solid *h) {
+  k_set_young_field<<<148 * 4, 256, 0, h->stream>>>(h->alphaN, h->nu, h->N, h->qfield);
+  LAUNCHED(h);
+  return setup_boundary(h);
 }
 
 lbm_status residual(lbm_solid *h, const double *a, const double *b, double &res) {
@@ -307,7 +360,7 @@ lbm_status objective_partials(lbm_solid *h) {
 void free_all(lbm_solid *h) {
   void *bufs[] = {h->fA, h->fB, h->pA, h->pB, h->g2, h->r2, h->dstar, h->obs, h->basis, h->Fbase,
                   h->type, h->regmask, h->bidx, h->Q, h->s, h->dQ, h->ds, h->bnodes,
-                  h->partial, h->dres};
+                  h->partial, h->dres, h->qfield, h->alphaN, h->gamf, h->bnode};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (h->hres) cudaFreeHost(h->hres);
@@ -343,7 +396,6 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
   if (d->control < LBM_CTRL_FORCE_FIELD || d->control > LBM_CTRL_YOUNG_FIELD) return LBM_ERR_ARG;
   if (d->kernel != LBM_KERNEL_AUTO && d->kernel != LBM_KERNEL_FP64) return LBM_ERR_ARG;
   if (d->control == LBM_CTRL_FORCE_BASIS2 && !d->force_basis) return LBM_ERR_ARG;
-  if (d->control == LBM_CTRL_YOUNG_FIELD) return LBM_ERR_ARG;  // per-node moduli: not built yet
   lbm_solid *h = new (std::nothrow) lbm_solid();
   if (!h) return LBM_ERR_OOM;
   h->nx = d->nx; h->ny = d->ny; h->N = (long)d->nx * d->ny; h->dx = d->dx;
@@ -358,6 +410,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
   std::vector<int> bidx(N, -1);
   std::vector<BoundaryNode> bn;
   std::vector<uint8_t> regm;
+  std::vector<int> bnode_h;
   if (h->periodic) {
     if (d->link_bc) return bail(LBM_ERR_ARG);
     if (d->node_mask)
@@ -402,6 +455,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
         bidx[n] = (int)bn.size();
         bn.push_back(b);
         regm.push_back(reg);
+        bnode_h.push_back((int)n);
       }
     }
     if (h->n_active == 0) return bail(LBM_ERR_ARG);
@@ -426,6 +480,15 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
   if (d->obs_mask) ALLOC(h->obs, sizeof(double) * N);
   if (d->control == LBM_CTRL_FORCE_BASIS2) ALLOC(h->basis, 2 * two);
   if (d->control >= LBM_CTRL_YOUNG_SCALAR) ALLOC(h->Fbase, two);
+  h->field = d->control == LBM_CTRL_YOUNG_FIELD;
+  if (h->field) {
+    ALLOC(h->qfield, 3 * sizeof(double) * N);
+    ALLOC(h->alphaN, sizeof(double) * N);
+    if (!h->periodic && h->nb) {
+      ALLOC(h->gamf, sizeof(double) * h->nb);
+      ALLOC(h->bnode, sizeof(int) * h->nb);
+    }
+  }
   if (!h->periodic) {
     ALLOC(h->type, N);
     ALLOC(h->bidx, sizeof(int) * N);
@@ -464,6 +527,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
     if (h->nb) {
       up(h->regmask, regm.data(), h->nb);
       up(h->bnodes, bn.data(), sizeof(BoundaryNode) * h->nb);
+      if (h->bnode) up(h->bnode, bnode_h.data(), sizeof(int) * h->nb);
     }
     h->bnd = Bounded{h->type, h->bidx, h->Q, h->s, h->regmask, h->dQ, h->ds};
   }
@@ -479,6 +543,14 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
 
   // ---- material and fixed force -----------------------------------------------------
   if (set_material(h, d->E) != LBM_OK) return bail(LBM_ERR_ARG);
+  if (h->field) {
+    // uniform start: alpha_n = sqrt(E) everywhere
+    std::vector<double> a0(N, std::sqrt(d->E));
+    up(h->alphaN, a0.data(), sizeof(double) * N);
+    if (e != cudaSuccess) return bail(LBM_ERR_CUDA);
+    h->fl = Field{h->qfield, h->gamf, h->alphaN, h->nu};
+    if (set_field(h) != LBM_OK) return bail(LBM_ERR_CUDA);
+  }
   if (h->Fbase) {
     if (d->force) {
       std::vector<double> F(d->force, d->force + 2 * N);
@@ -531,6 +603,31 @@ lbm_status lbm_solid_set_control(lbm_solid *h, const double *alpha, size_t n, in
       const lbm_status st = set_material(h, h->hres[0] * h->hres[0]);
       if (st) return st;
       h->alpha = h->hres[0];
+      break;
+    }
+    case LBM_CTRL_YOUNG_FIELD: {
+      if (n != (size_t)h->N) return fail(h, LBM_ERR_ARG, "YOUNG_FIELD control needs N values");
+      // validate on the host: every active modulus alpha_n^2 must give a valid material
+      std::vector<double> a(h->N), tp(h->N, 1.0);
+      CK(h, cudaMemcpyAsync(a.data(), alpha, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+      std::vector<uint8_t> ty;
+      if (!h->periodic) {
+        ty.resize(h->N);
+        CK(h, cudaMemcpyAsync(ty.data(), h->type, h->N, cudaMemcpyDeviceToHost, h->stream));
+      }
+      CK(h, cudaStreamSynchronize(h->stream));
+      for (long i = 0; i < h->N; ++i) {
+        if (!h->periodic && ty[i] == 0) continue;
+        Coef c{};
+        Material m{};
+        YoungDeriv yd{};
+        std::string why;
+        if (!material_coefs(a[i] * a[i], h->nu, !h->periodic && ty[i] == 2, h->has_neumann, c, m, yd, why))
+          return fail(h, LBM_ERR_ARG, "node " + std::to_string(i) + ": " + why);
+      }
+      CK(h, cudaMemcpyAsync(h->alphaN, alpha, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+      const lbm_status st = set_field(h);
+      if (st) return st;
       break;
     }
     default:
@@ -647,12 +744,22 @@ lbm_status lbm_solid_gradient(lbm_solid *h, double *grad, size_t n, int project)
     if (n != 1) return fail(h, LBM_ERR_ARG, "YOUNG_SCALAR gradient has 1 value");
     if (h->fcur_is_fs) return fail(h, LBM_ERR_STATE, "Young gradient needs a primal solve");
     if (h->periodic)
-      k_grad_young<false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->partial);
+      k_grad_young<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->fl, nullptr, h->partial);
     else
-      k_grad_young<true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->partial);
+      k_grad_young<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->fl, nullptr, h->partial);
     LAUNCHED(h);
     // E = alpha^2 (Eq. E_substitution): dJ/dalpha = 2 alpha dJ/dE
     return finish(h, h->nblocks2d, 1, 0, 2.0 * h->alpha, grad);
+  }
+  if (h->control == LBM_CTRL_YOUNG_FIELD) {
+    if (n != (size_t)h->N) return fail(h, LBM_ERR_ARG, "YOUNG_FIELD gradient has N values");
+    if (h->fcur_is_fs) return fail(h, LBM_ERR_STATE, "Young gradient needs a primal solve");
+    if (h->periodic)
+      k_grad_young<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->fl, grad, nullptr);
+    else
+      k_grad_young<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->pcur, h->grid, h->bnd, h->coef, h->yd, h->fl, grad, nullptr);
+    LAUNCHED(h);
+    return LBM_OK;
   }
   return fail(h, LBM_ERR_ARG, "gradient for this control kind is not built");
 }

@@ -50,11 +50,15 @@ def periodic_problem(nx, ny, seed):
     return F, dstar
 
 
+KERNELS = ["fp64", "auto"]  # FP64 pipe; integer-pipe fixed point for bulk nodes
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("nx,ny,E,nu,steps", CASES)
-def test_primal_adjoint_gradient_match_the_oracle(lbm_mod, nx, ny, E, nu, steps):
+def test_primal_adjoint_gradient_match_the_oracle(lbm_mod, nx, ny, E, nu, steps, kernel):
     F, dstar = periodic_problem(nx, ny, seed=nx + ny)
     dx = 1.0 / nx
-    s = lbm_mod.LBMSolid(nx, ny, dx, E, nu, periodic=True, control="force_field")
+    s = lbm_mod.LBMSolid(nx, ny, dx, E, nu, periodic=True, control="force_field", kernel=kernel)
     s.set_target(dev(dstar))
     s.set_control(dev(F))
     s.primal_solve(steps, fixed_steps=True)
@@ -80,14 +84,15 @@ def test_primal_adjoint_gradient_match_the_oracle(lbm_mod, nx, ny, E, nu, steps)
     s.close()
 
 
-def test_benchmark1_basis_gradient_matches_fad(lbm_mod):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_benchmark1_basis_gradient_matches_fad(lbm_mod, kernel):
     # F = alpha o F* (Eq. control_param_periodic) at alpha = (-1, -1), N_x = 20: the ALBM
     # gradient on the GPU equals the oracle's f-AD derivative (converged states).
     nx = 20
     m = I.periodic_manufactured(nx)
     basis = I.paper_scale_basis(m["Fstar"])
     s = lbm_mod.LBMSolid(nx, nx, m["dx"], I.PAPER_E, I.PAPER_NU, control="force_basis2",
-                         force_basis=basis.reshape(-1))
+                         force_basis=basis.reshape(-1), kernel=kernel)
     s.set_target(dev(m["dstar"]))
     s.set_control(dev([-1.0, -1.0]))
     steps = 30 * nx * nx
@@ -103,7 +108,8 @@ def test_benchmark1_basis_gradient_matches_fad(lbm_mod):
     s.close()
 
 
-def test_tiled_force_at_bench_size(lbm_mod):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_tiled_force_at_bench_size(lbm_mod, kernel):
     # Sampled parity at 4096^2 in the benchmark's launch configuration: a force with
     # period 16 gives a 16-periodic state (translation invariance), so every node of
     # the 4096^2 run must equal the 16^2 oracle run at the same position modulo 16.
@@ -116,7 +122,7 @@ def test_tiled_force_at_bench_size(lbm_mod):
     dstar = np.tile(dp, (1, reps, reps)).reshape(2, -1)
     E, nu, steps = 0.11, 0.8, 6
     dx = 1.0 / nx
-    s = lbm_mod.LBMSolid(nx, nx, dx, E, nu, control="force_field")
+    s = lbm_mod.LBMSolid(nx, nx, dx, E, nu, control="force_field", kernel=kernel)
     s.set_target(dev(dstar))
     s.set_control(dev(F))
     s.primal_solve(steps, fixed_steps=True)
@@ -137,6 +143,21 @@ def test_tiled_force_at_bench_size(lbm_mod):
     ref = phiS.reshape(8, P, P)[:, host(rows) % P][:, :, np.arange(nx) % P]
     assert rel_inf(sub, ref) <= POP_TOL
     s.close()
+
+
+def test_long_run_fixed_point_matches_fourier(lbm_mod):
+    # 30 N_x^2 sweeps (Section 4.2.2 protocol) with the integer-pipe kernel: the state
+    # reaches the exact per-wavevector fixed point, so rounding does not accumulate.
+    from oracle import fourier
+    nx = 48
+    m = I.periodic_manufactured(nx)
+    fF = fourier.periodic_fixed_point(nx, I.PAPER_E, I.PAPER_NU, m["Fstar"])
+    for kernel in KERNELS:
+        s = lbm_mod.LBMSolid(nx, nx, m["dx"], I.PAPER_E, I.PAPER_NU, kernel=kernel)
+        s.set_control(dev(m["Fstar"]))
+        s.primal_solve(30 * nx * nx, fixed_steps=True)
+        assert rel_inf(host(s.get_populations(0)).reshape(8, -1), fF) <= 1e-11, kernel
+        s.close()
 
 
 def test_stopping_rules_and_status_codes(lbm_mod):

@@ -46,11 +46,11 @@ def paper_plate(Nx, E=I.PLATE_E, nu=I.PLATE_NU):
     return geo, dstar, F * geo.active, wd, wT
 
 
-def make(lbm_mod, geo, wd, wT, E, nu, control="force_field", force=None):
+def make(lbm_mod, geo, wd, wT, E, nu, control="force_field", force=None, kernel="auto"):
     return lbm_mod.LBMSolid(geo.nx, geo.nx, geo.dx, E, nu, periodic=False,
                             node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
                             wall_n=geo.normal, obs=geo.active.astype(float), control=control,
-                            force=force)
+                            force=force, kernel=kernel)
 
 
 def ogrid(geo, wd, wT, nu):
@@ -58,11 +58,12 @@ def ogrid(geo, wd, wT, nu):
                        link=geo.link, wall_d=wd, wall_T=wT, wall_n=geo.normal)
 
 
+@pytest.mark.parametrize("kernel", ["fp64", "auto"])
 @pytest.mark.parametrize("Nx,E,nu,steps", [(12, I.PLATE_E, I.PLATE_NU, 30),
                                            (20, 1.0, 0.3, 45), (37, 0.15, 0.7, 23)])
-def test_plate_primal_adjoint_force_gradient(lbm_mod, Nx, E, nu, steps):
+def test_plate_primal_adjoint_force_gradient(lbm_mod, Nx, E, nu, steps, kernel):
     geo, dstar, F, wd, wT = paper_plate(Nx, E=E, nu=nu)
-    s = make(lbm_mod, geo, wd, wT, E, nu)
+    s = make(lbm_mod, geo, wd, wT, E, nu, kernel=kernel)
     s.set_target(dev(dstar))
     s.set_control(dev(F))
     s.primal_solve(steps, fixed_steps=True)
