@@ -48,6 +48,19 @@ def peaks():
         return 6400.0, 2032.0, "fallback"
 
 
+def reduce_max_over_ranks(value: float, dist_mod, device) -> float:
+    """Max of a per-rank scalar (the timed region's duration) over all ranks."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(lups_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return lups_per_rank * world / (ms_max * 1e-3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -129,6 +142,59 @@ def traffic_from_profiles(kernel: str):
     return None
 
 
+def time_to_gradient(torch, lbm, I, reps: int = 3):
+    """Wall time of one gradient evaluation at fixed accuracy (primal to residual 1e-10,
+    objective, adjoint to residual 1e-10, gradient) on the small workloads; min of reps.
+    Residual: max|f_C(t) - f_C(t-1)| / max|f_C(t)|, checked every 64 sweeps."""
+    out = {}
+
+    def timed(s, ctrl, n_grad):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.set_control(ctrl)
+            ip = s.primal_solve(2_000_000, tol=1e-10, criterion=1, check_every=64)
+            s.objective()
+            ia = s.adjoint_solve(2_000_000, tol=1e-10, criterion=1, check_every=64)
+            g = s.gradient()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if best is None or dt < best[0]:
+                best = (dt, ip.steps, ia.steps)
+        dt, ps, as_ = best
+        return {"ms": 1e3 * dt, "primal_sweeps": ps, "adjoint_sweeps": as_,
+                "us_per_sweep": 1e6 * dt / (ps + as_)}
+
+    # two-amplitude workload, 32^2, lambda = mu = 1, at alpha = (0.5, 0.25)
+    c = I.config_amplitudes(32)
+    s = lbm.LBMSolid(32, 32, c["dx"], c["E"], c["nu"], control="force_basis2",
+                     force_basis=c["basis"].reshape(-1))
+    s.set_target(torch.as_tensor(c["dstar"].ravel(), device="cuda"))
+    out["amplitudes_32"] = timed(s, torch.tensor([0.5, 0.25], dtype=torch.float64, device="cuda"), 2)
+    s.close()
+    # distributed force control, 80^2 (12,800 controls), at half the reference force
+    c = I.config_amplitudes(80)
+    F = 0.5 * np.tensordot([1.0, 0.5], c["basis"], axes=1)
+    s = lbm.LBMSolid(80, 80, c["dx"], c["E"], c["nu"], control="force_field")
+    s.set_target(torch.as_tensor(c["dstar"].ravel(), device="cuda"))
+    out["force_field_80"] = timed(s, torch.as_tensor(F.ravel(), device="cuda"), 12800)
+    s.close()
+    # elliptic plate, N_x = 64, scalar Young's modulus at E = 0.15 (E* = 0.1)
+    geo = I.plate_geometry(64)
+    dstar, sigma, Fp = I.plate_manufactured(geo.X, geo.Y)
+    wd, wT = I.plate_wall_data(geo, dstar, sigma)
+    s = lbm.LBMSolid(geo.nx, geo.nx, geo.dx, I.PLATE_E, I.PLATE_NU, periodic=False,
+                     node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
+                     wall_n=geo.normal, obs=geo.active.astype(float), control="young_scalar",
+                     force=Fp * geo.active)
+    s.set_target(torch.as_tensor(dstar.ravel(), device="cuda"))
+    out["plate_young_64"] = timed(s, torch.tensor([np.sqrt(0.15)], dtype=torch.float64,
+                                                  device="cuda"), 1)
+    s.close()
+    return out
+
+
 def cpu_baseline(seconds_target: float = 12.0):
     """The oracle as it stands, single thread, on a bounded sample: 512^2, primal then
     adjoint sweeps of the same workload kind."""
@@ -139,13 +205,7 @@ def cpu_baseline(seconds_target: float = 12.0):
     dstar = np.random.default_rng(1).standard_normal((2, nx * nx)) * 1e-2
     g = oracle.Grid(nx, nx, 1.0 / nx, 1.0 / 3.0)
     E = 8.0 / 3.0
-    t0 = time.perf_counter()
-    sweeps = 2
-    fS = oracle.primal(g, E, F, sweeps)
-    oracle.adjoint(g, E, F, fS, dstar, sweeps)
-    t1 = time.perf_counter() - t0
-    # scale to ~seconds_target of work
-    sweeps = max(2, int(sweeps * seconds_target / max(t1, 1e-3) / 2))
+    sweeps = 100  # about 12 s of single-thread work on the oracle
     t0 = time.perf_counter()
     fS = oracle.primal(g, E, F, sweeps)
     oracle.adjoint(g, E, F, fS, dstar, sweeps)
@@ -202,6 +262,7 @@ def main():
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--sweeps", type=int, default=100, help="primal (and adjoint) sweeps per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gradient runs")
     ap.add_argument("--kernel", default="auto", choices=["auto", "fp64"],
                     help="sweep arithmetic: integer-pipe fixed point (auto) or FP64 pipe")
     args = ap.parse_args()
@@ -270,14 +331,11 @@ def main():
     clocks = clk.stop() if clk else None
     ms = t_start.elapsed_time(t_end)
     if pg:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = reduce_max_over_ranks(ms, pg, "cuda")
         pg.barrier()
     primal_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / (args.steps * K)
     adjoint_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / (args.steps * K)
-    lups = 2.0 * K * N * args.steps * world
-    value = lups / (ms * 1e-3) / 1e6
+    value = job_mlups(2.0 * K * N * args.steps, world, ms)
 
     # end-to-end through the public API with host buffers: control H2D, gradient D2H
     F_host = torch.as_tensor(F.ravel()).pin_memory()
@@ -343,6 +401,8 @@ def main():
         t2 = e0.elapsed_time(e1) / 20
         out["fp64_pipe_variant"] = {"primal_sweep_ms": t2, "primal_glups": N / (t2 * 1e-3) / 1e9}
         s = s2
+    if rank == 0 and world == 1 and not args.no_ttg:
+        out["time_to_gradient"] = time_to_gradient(torch, lbm, I)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:

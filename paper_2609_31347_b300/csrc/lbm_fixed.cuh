@@ -20,8 +20,12 @@
 //
 // Every result is within a few units of 2^-56 of the node's largest input of the exact
 // value (binary64 rounding of the FP64-pipe variant is 2^-53 of each operand), far
-// inside the 1e-11 parity bound.  Nodes whose largest exponent exceeds 2000 (values
-// near overflow, Inf, NaN) take the FP64-pipe path so that Inf/NaN propagate.
+// inside the 1e-11 parity bound.  The fixed-point path is taken only when the node's
+// largest biased exponent E lies in [kEmin, kEmax] (largest input between 2^-923 and
+// 2^57): then every shifted input keeps a positive exponent field, zeros and
+// subnormals shift to values below 1 that truncate to 0, and every nonzero result has
+// a normal exponent, so no per-value range test is needed.  Other nodes (all-zero
+// nodes, extreme magnitudes, Inf, NaN) take the FP64-pipe path.
 #pragma once
 #include "lbm_device.cuh"
 
@@ -38,56 +42,53 @@ __device__ __forceinline__ long long mulfix(long long v, FixC c) {
   return (long long)vh * c.hi + (t >> 31);
 }
 
+constexpr int kEmin = 100, kEmax = 1079;
+
 __device__ __forceinline__ int exp_of(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
 
-// x 2^sh truncated toward zero (0 for zero / subnormal inputs or results below the
-// smallest normal number).
-__device__ __forceinline__ long long to_fix(double x, int ex, int sh) {
-  const int hi = __double2hiint(x), lo = __double2loint(x);
-  const bool keep = (ex != 0) && (ex + sh > 0);
-  const double y = __hiloint2double(keep ? hi + (int)((unsigned)sh << 20) : 0, keep ? lo : 0);
-  return __double2ll_rz(y);
+// x 2^sh truncated toward zero, sh = 1079 - E >= 0 (E in [kEmin, kEmax]): adding sh to
+// the exponent field is exact for normal x; a zero or subnormal x becomes a value below
+// 2^(sh-1022) <= 2^-42 < 1, which truncates to 0.
+__device__ __forceinline__ long long to_fix(double x, int sh20) {
+  return __double2ll_rz(__hiloint2double(__double2hiint(x) + sh20, __double2loint(x)));
 }
 
-// v 2^(E-1079) rounded to nearest (ties away from zero); tiny results flush to 0.
+// v 2^(E-1079) rounded to nearest (ties away from zero).  With E >= kEmin every
+// nonzero |v| >= 1 gives a normal result (biased exponent E + 7 - lz >= 43).
 __device__ __forceinline__ double from_fix(long long v, int E) {
   const unsigned long long s = (unsigned long long)(v >> 63);
   const unsigned long long a = ((unsigned long long)v ^ s) - s;
   const int lz = __clzll((long long)a);
-  const int ef = E + 7 - lz;
   const unsigned long long m = a << (lz & 63);
   unsigned long long bits =
-      ((unsigned long long)(unsigned)(ef - 1) << 52) + (m >> 11) + ((m >> 10) & 1ull);
+      ((unsigned long long)(unsigned)(E + 6 - lz) << 52) + (m >> 11) + ((m >> 10) & 1ull);
   bits |= s & 0x8000000000000000ull;
-  if (a == 0 || ef <= 0) bits = 0;
-  return __longlong_as_double((long long)bits);
+  return __longlong_as_double(a == 0 ? 0ll : (long long)bits);
 }
 
-__device__ __forceinline__ int max_exp10(const double (&f)[8], double a, double b, int (&e)[10]) {
+// Largest biased exponent of the node's ten inputs: the exponent field is monotone in
+// |x|, so take the max of the high words with the sign bit cleared, then extract once.
+__device__ __forceinline__ int max_exp10(const double (&f)[8], double a, double b) {
+  int m = __double2hiint(a) & 0x7fffffff;
+  m = max(m, __double2hiint(b) & 0x7fffffff);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) e[k] = exp_of(f[k]);
-  e[8] = exp_of(a);
-  e[9] = exp_of(b);
-  int E = e[0];
-#pragma unroll
-  for (int k = 1; k < 10; ++k) E = max(E, e[k]);
-  return E;
+  for (int k = 0; k < 8; ++k) m = max(m, __double2hiint(f[k]) & 0x7fffffff);
+  return m >> 20;
 }
 
 // Bulk collision in fixed point (same map as collide<false>).  Returns false when the
-// node must take the FP64-pipe path (largest exponent > 2000).
+// node must take the FP64-pipe path (largest exponent outside [kEmin, kEmax]).
 template <bool MON>
 __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, double qy,
                                             const CoefFix &c, double (&o)[8], double &dx_,
                                             double &dy_) {
-  int e[10];
-  const int E = max_exp10(f, qx, qy, e);
-  if (E > 2000) return false;
-  const int sh = 1079 - E;
+  const int E = max_exp10(f, qx, qy);
+  if (E < kEmin || E > kEmax) return false;
+  const int sh20 = (1079 - E) << 20;
   long long F[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) F[k] = to_fix(f[k], e[k], sh);
-  const long long QX = to_fix(qx, e[8], sh), QY = to_fix(qy, e[9], sh);
+  for (int k = 0; k < 8; ++k) F[k] = to_fix(f[k], sh20);
+  const long long QX = to_fix(qx, sh20), QY = to_fix(qy, sh20);
   const long long a1 = F[0] + F[2], b1 = F[0] - F[2];
   const long long a2 = F[1] + F[3], b2 = F[1] - F[3];
   const long long a3 = F[4] + F[6], b3 = F[4] - F[6];
@@ -124,14 +125,13 @@ template <bool MON>
 __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, double ry,
                                               const CoefFix &c, double (&o)[8], double &ax,
                                               double &ay) {
-  int e[10];
-  const int E = max_exp10(p, rx, ry, e);
-  if (E > 2000) return false;
-  const int sh = 1079 - E;
+  const int E = max_exp10(p, rx, ry);
+  if (E < kEmin || E > kEmax) return false;
+  const int sh20 = (1079 - E) << 20;
   long long P[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) P[k] = to_fix(p[k], e[k], sh);
-  const long long RX = to_fix(rx, e[8], sh), RY = to_fix(ry, e[9], sh);
+  for (int k = 0; k < 8; ++k) P[k] = to_fix(p[k], sh20);
+  const long long RX = to_fix(rx, sh20), RY = to_fix(ry, sh20);
   const long long A1 = P[0] + P[2], B1 = P[0] - P[2];
   const long long A2 = P[1] + P[3], B2 = P[1] - P[3];
   const long long A3 = P[4] + P[6], B3 = P[4] - P[6];

@@ -45,6 +45,17 @@ struct lbm_solid {
   int *bnode = nullptr;
   Field fl{};
   bool field = false;
+  // CUDA graphs of sweep chunks (launch overhead dominates small lattices): captured on
+  // a private stream, replayed on the caller's stream, rebuilt when kernel parameters
+  // passed by value change (version).
+  cudaStream_t cap = nullptr;
+  struct GraphEnt {
+    int kind, parity, mon;
+    long k, version;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEnt> graphs;
+  long version = 0;
   BoundaryNode *bnodes = nullptr;
   long nb = 0;
   double *partial = nullptr;
@@ -154,6 +165,7 @@ lbm_status set_material(lbm_solid *h, double E) {
   h->coef = c;
   h->mat = m;
   h->yd = yd;
+  ++h->version;  // graphs bake Coef in as a kernel parameter
   h->E = E;
   return setup_boundary(h);
 }
@@ -244,6 +256,94 @@ lbm_status adjoint_sweep(lbm_solid *h, bool monitor) {
   return LBM_OK;
 }
 
+constexpr long kGraphMin = 4, kGraphMax = 128;
+
+// Sweeps that are replayed from a captured graph: k plain sweeps starting from buffer
+// parity `parity`, the last one with monitor partials when mon is set.
+lbm_status graph_for(lbm_solid *h, int kind, long k, bool mon, cudaGraphExec_t &exec) {
+  const int parity = kind == 0 ? (h->fcur == h->fA ? 0 : 1) : (h->pcur == h->pA ? 0 : 1);
+  for (const auto &g : h->graphs)
+    if (g.kind == kind && g.k == k && g.parity == parity && g.mon == (int)mon &&
+        g.version == h->version) {
+      exec = g.exec;
+      return LBM_OK;
+    }
+  if (!h->cap) CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  double *f0 = h->fcur, *f1 = h->fnext, *p0 = h->pcur, *p1 = h->pnext;
+  cudaStream_t user = h->stream;
+  const long launches = h->launches;
+  CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  h->stream = h->cap;
+  lbm_status st = LBM_OK;
+  for (long i = 0; i < k && st == LBM_OK; ++i) {
+    const bool m = mon && i == k - 1;
+    // the kernels themselves (primal_sweep / adjoint_sweep without the launch check,
+    // which would see the capture state)
+    if (kind == 0) {
+      if (h->field) launch_primal<0, true>(h, m);
+      else if (h->kernel == LBM_KERNEL_FP64) launch_primal<0, false>(h, m);
+      else launch_primal<1, false>(h, m);
+      std::swap(h->fcur, h->fnext);
+    } else {
+      if (h->field) launch_adjoint<0, true>(h, m);
+      else if (h->kernel == LBM_KERNEL_FP64) launch_adjoint<0, false>(h, m);
+      else launch_adjoint<1, false>(h, m);
+      std::swap(h->pcur, h->pnext);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+  h->stream = user;
+  h->fcur = f0; h->fnext = f1; h->pcur = p0; h->pnext = p1;
+  h->launches = launches;
+  if (ec != cudaSuccess || !graph)
+    return fail(h, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess)
+    return fail(h, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  if (h->graphs.size() >= 16) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(lbm_solid::GraphEnt{kind, parity, (int)mon, k, h->version, ex});
+  exec = ex;
+  return st;
+}
+
+// k sweeps (kind 0 primal, 1 adjoint), monitor partials on the last one if mon.
+lbm_status run_sweeps(lbm_solid *h, int kind, long k, bool mon) {
+  if (kind == 0 && h->fcur_is_fs && k > 0) {  // first sweep from an explicit f_S
+    lbm_status st = primal_sweep(h, false);
+    if (st) return st;
+    --k;
+  }
+  while (k > 0) {
+    long c = k > kGraphMax ? kGraphMax : k;
+    if (k > kGraphMax && k - c < kGraphMin) c = k - kGraphMin;  // keep the tail graphable
+    const bool m = mon && c == k;
+    if (c < kGraphMin) {
+      for (long i = 0; i < c; ++i) {
+        lbm_status st = kind == 0 ? primal_sweep(h, m && i == c - 1) : adjoint_sweep(h, m && i == c - 1);
+        if (st) return st;
+      }
+    } else {
+      cudaGraphExec_t ex = nullptr;
+      lbm_status st = graph_for(h, kind, c, m, ex);
+      if (st) return st;
+      CK(h, cudaGraphLaunch(ex, h->stream));
+      h->launches += c;
+      if (c & 1) {
+        if (kind == 0) std::swap(h->fcur, h->fnext);
+        else std::swap(h->pcur, h->pnext);
+      }
+    }
+    k -= c;
+  }
+  return LBM_OK;
+}
+
 lbm_status set_field(lbm_solid *h) {
   k_set_young_field<<<148 * 4, 256, 0, h->stream>>>(h->alphaN, h->nu, h->N, h->qfield);
   LAUNCHED(h);
@@ -265,31 +365,29 @@ lbm_status residual(lbm_solid *h, const double *a, const double *b, double &res)
 }
 
 // Shared stopping loop of the primal and adjoint solves.
-template <class Sweep, class Resid>
-lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *info, Sweep sweep,
-                      Resid resid, bool can_monitor_first) {
+template <class Resid>
+lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *info, int kind,
+                      Resid resid) {
   const auto t0 = std::chrono::steady_clock::now();
   long steps = 0;
   double metric = 0.0;
   lbm_status result = LBM_OK;
   if (o->fixed_steps) {
-    for (; steps < o->max_steps; ++steps) {
-      lbm_status st = sweep(false);
-      if (st) return st;
-    }
+    lbm_status st = run_sweeps(h, kind, o->max_steps, false);
+    if (st) return st;
+    steps = o->max_steps;
   } else {
     std::deque<double> win;
     bool done = false;
     while (!done && steps < o->max_steps) {
       long k = o->check_every;
       if (k > o->max_steps - steps) k = o->max_steps - steps;
-      for (long i = 0; i < k; ++i) {
-        const bool last = (i == k - 1);
-        lbm_status st = sweep(last && o->criterion == 0);
-        if (st) return st;
-        ++steps;
-      }
-      if (steps < 2 && !can_monitor_first) continue;
+      // a chunk whose only sweep is the collide-only first sweep has no monitor value
+      const bool first_only = kind == 0 && h->fcur_is_fs && k == 1;
+      lbm_status st = run_sweeps(h, kind, k, o->criterion == 0);
+      if (st) return st;
+      steps += k;
+      if (steps < 2 || first_only) continue;
       double v = 0.0;
       if (o->criterion == 0) {
         lbm_status st = finish(h, h->nblocks2d, 1, 0, h->n_active ? 1.0 / h->n_active : 0.0, h->dres);
@@ -574,6 +672,9 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
 lbm_status lbm_solid_destroy(lbm_solid *h) {
   if (!h) return LBM_ERR_ARG;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  if (h->cap) cudaStreamDestroy(h->cap);
   free_all(h);
   delete h;
   return LBM_OK;
@@ -672,9 +773,8 @@ lbm_status lbm_solid_primal_solve(lbm_solid *h, const lbm_solve_opts *o, lbm_sol
   if (st) return st;
   h->adjoint_valid = false;
   h->adj_warm = false;
-  auto sweep = [h](bool mon) { return primal_sweep(h, mon); };
   auto resid = [h](double &v) { return residual(h, h->fcur, h->fnext, v); };
-  return solve_loop(h, o, info, sweep, resid, false);
+  return solve_loop(h, o, info, 0, resid);
 }
 
 lbm_status lbm_solid_objective(lbm_solid *h, double *J) {
@@ -700,9 +800,8 @@ lbm_status lbm_solid_adjoint_solve(lbm_solid *h, const lbm_solve_opts *o, lbm_so
   if ((st = objective_partials(h))) return st;
   if (!h->adj_warm) CK(h, cudaMemsetAsync(h->pcur, 0, sizeof(double) * 8 * h->N, h->stream));
   h->adj_warm = false;
-  auto sweep = [h](bool mon) { return adjoint_sweep(h, mon); };
   auto resid = [h](double &v) { return residual(h, h->pcur, h->pnext, v); };
-  st = solve_loop(h, o, info, sweep, resid, false);
+  st = solve_loop(h, o, info, 1, resid);
   if (st == LBM_OK || st == LBM_ERR_NOT_CONVERGED) h->adjoint_valid = true;
   return st;
 }

@@ -136,3 +136,38 @@ def test_plate_rejects_inconsistent_links(lbm_mod):
                          node_mask=geo.active, link_bc=bad, wall_d=wd, wall_T=wT,
                          wall_n=geo.normal)
     assert e.value.status == lbm_mod.LBM_ERR_ARG
+
+
+def test_plate_primal_convergence_order(lbm_mod):
+    # Section 4.3.2 protocol: N_x in {32, 64, 128, 256}, 40 N_x^2 sweeps from f_S = 0,
+    # errors against the manufactured solution on Omega^E.  The paper's boundary rules
+    # are not given, so only the first-order character is pinned (printed EOCs 1.06 /
+    # 1.07 for the displacement, Table golden/plate_primal_eoc.txt).
+    from tests.conftest import golden
+    gd = golden("plate_primal_eoc.txt")
+    nxs, ed2, edi, es2 = [32, 64, 128, 256], [], [], []
+    for Nx in nxs:
+        geo, dstar, F, wd, wT = paper_plate(Nx)
+        s = make(lbm_mod, geo, wd, wT, I.PLATE_E, I.PLATE_NU)
+        s.set_control(dev(F))
+        s.primal_solve(40 * Nx * Nx, fixed_steps=True)
+        act = geo.active == 1
+        d = host(s.displacement()).reshape(2, -1)
+        fS = host(s.get_populations(0)).reshape(8, -1)
+        s.close()
+        g = ogrid(geo, wd, wT, I.PLATE_NU)
+        _, sigma, _ = I.plate_manufactured(geo.X, geo.Y)
+        sg = oracle.stress(g, I.PLATE_E, fS, F)
+        e = (d - dstar)[:, act]
+        ed2.append(oracle.norm_L2(e, geo.dx) / oracle.norm_L2(dstar[:, act], geo.dx))
+        edi.append(oracle.norm_Linf(e) / oracle.norm_Linf(dstar[:, act]))
+        fro = oracle.stress_frobenius_rows
+        es2.append(oracle.norm_L2(fro(sg - sigma)[:, act], geo.dx) /
+                   oracle.norm_L2(fro(sigma)[:, act], geo.dx))
+    eoc_d2, eoc_di = oracle.eoc(nxs, ed2), oracle.eoc(nxs, edi)
+    eoc_s2 = oracle.eoc(nxs, es2)
+    print("plate errors d L2", ed2, "d Linf", edi, "sigma L2", es2)
+    print("plate EOC d L2 %.3f (paper %.2f), d Linf %.3f (paper %.2f), sigma L2 %.3f (paper %.2f)"
+          % (eoc_d2, gd["eoc_d_L2"][0], eoc_di, gd["eoc_d_Linf"][0], eoc_s2, gd["eoc_sigma_L2"][0]))
+    assert ed2[-1] < ed2[0]
+    assert 0.6 <= eoc_d2 <= 2.2
