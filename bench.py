@@ -183,7 +183,7 @@ def time_to_gradient(torch, lbm, I, reps: int = 3):
     # elliptic plate, N_x = 64, scalar Young's modulus at E = 0.15 (E* = 0.1)
     geo = I.plate_geometry(64)
     dstar, sigma, Fp = I.plate_manufactured(geo.X, geo.Y)
-    wd, wT = I.plate_wall_data(geo, dstar, sigma)
+    wd, wT = I.plate_wall_data(geo)
     s = lbm.LBMSolid(geo.nx, geo.nx, geo.dx, I.PLATE_E, I.PLATE_NU, periodic=False,
                      node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
                      wall_n=geo.normal, obs=geo.active.astype(float), control="young_scalar",
@@ -192,6 +192,142 @@ def time_to_gradient(torch, lbm, I, reps: int = 3):
     out["plate_young_64"] = timed(s, torch.tensor([np.sqrt(0.15)], dtype=torch.float64,
                                                   device="cuda"), 1)
     s.close()
+    return out
+
+
+def batch_throughput(torch, lbm, I, count: int = 256, sweeps: int = 20, seed: int = 1):
+    """Batched workload: `count` periodic instances, side ~ U{64..1024} (seed 1), each with
+    its own 8-mode force; primal and adjoint sweeps of all instances, one launch per sweep
+    replayed from CUDA graphs, tile width autotuned.  Returns throughput and HBM rate."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(64, 1025, size=count)
+    b = lbm.LBMBatch([(int(n), int(n)) for n in sides], 8.0 / 3.0, 1.0 / 3.0)
+    F = torch.empty(2 * b.total, dtype=torch.float64, device="cuda")
+    D = torch.empty(2 * b.total, dtype=torch.float64, device="cuda")
+    for i, n in enumerate(sides):
+        o = b.offsets[i]
+        F[2 * o:2 * (o + n * n)] = torch.as_tensor(
+            I.fourier_force(int(n), seed=100 + i).ravel(), device="cuda")
+        D[2 * o:2 * (o + n * n)] = 1e-2 * torch.randn(2 * int(n) * int(n), dtype=torch.float64,
+                                                      device="cuda")
+    b.set_target(D)
+    b.set_force(F)
+    bx = b.tune(8)
+    b.set_force(F)
+    b.primal(8)
+    b.adjoint(8)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    b.primal(sweeps)
+    e[1].record(stream)
+    b.adjoint(sweeps)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    tp, ta = e[0].elapsed_time(e[1]) / sweeps, e[1].elapsed_time(e[2]) / sweeps
+    out = {"instances": count, "nodes": b.total, "tile_width": bx,
+           "primal_sweep_ms": tp, "adjoint_sweep_ms": ta,
+           "glups": 2 * b.total / ((tp + ta) * 1e-3) / 1e9,
+           "primal_hbm_gbs": BYTES_PER_LUP * b.total / (tp * 1e-3) / 1e9}
+    b.close()
+    return out
+
+
+def warm_start(torch, lbm, I, samples: int = 2048, steps: int = 1500, seed: int = 1):
+    """Learned warm start (not in the paper): primal and adjoint networks trained on
+    `samples` solver-generated 128^2 steady states each (random 8-mode fields), then
+    iterations and wall time to residual 1e-10 cold vs warm on held-out 8-mode controls
+    at 128^2 and 512^2 (the 128^2 networks used at 4x resolution), and one L-BFGS
+    identification of a 128^2 distributed force (32,768 controls) run cold and warm."""
+    from paper_2609_31347_b300 import gbo
+    from paper_2609_31347_b300 import warmstart as W
+    E, nu = 8.0 / 3.0, 1.0 / 3.0
+    out = {"train": {}}
+    nets = {}
+    for kind in ("primal", "adjoint"):
+        w = W.WarmStartNet(kind, nx=128, E=E, nu=nu, seed=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, T = w.generate(samples, sweeps=5000, seed=seed)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        log = w.fit(X, T, steps=steps, lr=3e-4)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        del X, T
+        Xh, Th = w.generate(64, sweeps=5000, seed=seed + 1000)
+        out["train"][kind] = {"samples": samples, "generate_s": t1 - t0, "steps": steps,
+                              "train_s": t2 - t1, "ms_per_step": 1e3 * (t2 - t1) / steps,
+                              "loss_first": log[0][1], "loss_last": log[-1][1],
+                              "heldout_rel_err": w.evaluate(Xh, Th)}
+        nets[kind] = w
+
+    def to_gradient(nx, F, dstar, warm):
+        s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu)
+        s.set_target(dstar)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_control(F)
+        if warm:
+            f0 = torch.empty(8 * nx * nx, dtype=torch.float64, device="cuda")
+            nets["primal"].predict(F, f0, nx_fine=nx)
+            s.set_populations(0, f0)
+        ip = s.primal_solve(4_000_000, tol=1e-10, criterion=1, check_every=64)
+        if warm:
+            p0 = torch.empty(8 * nx * nx, dtype=torch.float64, device="cuda")
+            nets["adjoint"].predict(s.adjoint_source(), p0, nx_fine=nx)
+            s.set_populations(2, p0)
+        ia = s.adjoint_solve(4_000_000, tol=1e-10, criterion=1, check_every=64)
+        g = s.gradient()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        s.close()
+        return {"ms": 1e3 * dt, "primal_sweeps": ip.steps, "adjoint_sweeps": ia.steps}, g
+
+    for nx in (128, 512):
+        rows = {"cold": [], "warm": []}
+        for k in range(3):
+            F = I.fourier_fields(1, nx, seed=7000 + k, kmax=4).reshape(-1).contiguous()
+            dstar = 1e-2 * I.fourier_fields(1, nx, seed=8000 + k, kmax=4).reshape(-1).contiguous()
+            rc, gc = to_gradient(nx, F, dstar, False)
+            rw, gw = to_gradient(nx, F, dstar, True)
+            rw["grad_rel_diff"] = float((gw - gc).abs().max() / gc.abs().max())
+            rows["cold"].append(rc)
+            rows["warm"].append(rw)
+        agg = {}
+        for kind, rs in rows.items():
+            agg[kind] = {key: float(np.mean([r[key] for r in rs])) for key in rs[0]}
+        agg["speedup"] = agg["cold"]["ms"] / agg["warm"]["ms"]
+        out["time_to_gradient_%d" % nx] = agg
+
+    # identification: distributed force at 128^2 towards the displacement of an 8-mode force
+    nx = 128
+    Fstar = I.fourier_fields(1, nx, seed=21, kmax=4).reshape(-1).contiguous()
+    s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu)
+    s.set_control(Fstar)
+    s.primal_solve(4_000_000, tol=1e-12, criterion=1, check_every=64)
+    dstar = s.displacement()
+    s.close()
+    gres = {}
+    for name, warm in (("cold", None), ("warm", W.WarmStarter(nets["primal"], nets["adjoint"]))):
+        s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu)
+        s.set_target(dstar)
+        fg = gbo.make_fg(s, gbo.SolveOpts(tol=1e-10), gbo.SolveOpts(tol=1e-10), project=True,
+                         warm=warm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = gbo.lbfgs(fg, torch.zeros_like(Fstar), m_max=15, eps=1e-14)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        err = float(torch.linalg.vector_norm(r.alpha - Fstar) / torch.linalg.vector_norm(Fstar))
+        gres[name] = {"s": dt, "control_rel_err": err, "J": r.J, "lbfgs_steps": r.steps,
+                      "sweeps": s.sweeps.get("primal_solve", 0) + s.sweeps.get("adjoint_solve", 0)}
+        s.close()
+    gres["speedup"] = gres["cold"]["s"] / gres["warm"]["s"]
+    out["identification_128"] = gres
+    for w in nets.values():
+        w.net.close()
     return out
 
 
@@ -263,6 +399,10 @@ def main():
     ap.add_argument("--sweeps", type=int, default=100, help="primal (and adjoint) sweeps per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gradient runs")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--warm-samples", type=int, default=2048,
+                    help="training states per network for the warm start")
     ap.add_argument("--kernel", default="auto", choices=["auto", "fp64"],
                     help="sweep arithmetic: integer-pipe fixed point (auto) or FP64 pipe")
     args = ap.parse_args()
@@ -403,6 +543,11 @@ def main():
         s = s2
     if rank == 0 and world == 1 and not args.no_ttg:
         out["time_to_gradient"] = time_to_gradient(torch, lbm, I)
+    if rank == 0 and world == 1 and not args.no_batch:
+        s.close()
+        out["batch_256"] = batch_throughput(torch, lbm, I)
+    if rank == 0 and world == 1 and not args.no_warm:
+        out["warm_start"] = warm_start(torch, lbm, I, samples=args.warm_samples)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -139,11 +139,17 @@ lbm_status lbm_solid_primal_solve(lbm_solid *h, const lbm_solve_opts *opts,
 /* Objective J of Eq. discrete_J at the current primal state (needs a target). */
 lbm_status lbm_solid_objective(lbm_solid *h, double *J_host);
 
-/* Adjoint solve (Algorithm 1): phi_C(0) = 0, iterate Eq. adjoint_iteration at the
-   current primal state.  Needs set_target and a primal solve after the last
-   set_control. */
+/* Adjoint solve (Algorithm 1): phi_C(0) = 0 (or the phi_C given by
+   set_populations(which = 2) since the last adjoint solve), iterate Eq.
+   adjoint_iteration at the current primal state.  Needs set_target and a primal solve
+   after the last set_control. */
 lbm_status lbm_solid_adjoint_solve(lbm_solid *h, const lbm_solve_opts *opts,
                                    lbm_solve_info *info);
+
+/* The nodal adjoint source field r = (dx^2 / Cbar) w (d - d*) of the current primal
+   state (2N values, device; the adjoint's constant term is j_k = r . c_k, Eq. j of
+   Algorithm 1).  Needs set_target.  Used to warm-start the adjoint. */
+lbm_status lbm_solid_adjoint_source(lbm_solid *h, double *r_dev);
 
 /* Gradient dJ/dalpha (Eq. optimality) from the current primal and adjoint states,
    written to grad_dev (device, n values as in set_control).  project_zero_mean
@@ -151,6 +157,19 @@ lbm_status lbm_solid_adjoint_solve(lbm_solid *h, const lbm_solve_opts *opts,
    FORCE_FIELD only). */
 lbm_status lbm_solid_gradient(lbm_solid *h, double *grad_dev, size_t n,
                               int project_zero_mean);
+
+/* Forward-mode derivative (f-AD, Eq. fAD) of J along a control direction, at the
+   current (converged) primal state: the tangent populations are iterated from zero with
+   the differentiated collide + stream step (the primal state held fixed) until opts'
+   rule holds, then dJ = sum_n obs (d - d*) . d-dot dx^2 / Cbar is written to dJ_host.
+   seed_dev: device direction with n = 2N (FORCE_FIELD), 2 (FORCE_BASIS2) or 1
+   (YOUNG_SCALAR, direction in alpha; E = alpha^2).  Not built for YOUNG_FIELD
+   (LBM_ERR_ARG).  Needs set_target and a primal solve (LBM_ERR_STATE); allocates two
+   population buffers on first use.  An independent check of the adjoint gradient: one
+   tangent solve per control direction. */
+lbm_status lbm_solid_tangent(lbm_solid *h, const double *seed_dev, size_t n,
+                             const lbm_solve_opts *opts, double *dJ_host,
+                             lbm_solve_info *info);
 
 /* Populations: which = 0 primal f_S, 1 adjoint phi_S, 2 adjoint phi_C; 8N device
    doubles.  set_populations(0) sets f_S (warm start / checkpoint restore);
@@ -164,6 +183,124 @@ lbm_status lbm_solid_displacement(lbm_solid *h, double *d_dev);
 
 /* Number of kernel launches this handle has issued (for launch accounting). */
 long lbm_solid_launch_count(const lbm_solid *h);
+
+/* ---- Batches of periodic lattices -------------------------------------------------
+ * Many periodic instances of uneven size (e.g. independent identifications, or the
+ * node-wise finite-difference perturbations of one problem) advanced together: every
+ * sweep is ONE kernel launch over all instances' tiles, and runs of sweeps are replayed
+ * from CUDA graphs.  Same collision, adjoint and gradient as the single-lattice path
+ * (Section 3.1, Eq. adjoint_iteration, Eq. optimality for the nodal force control), so
+ * an instance reproduces a single-lattice handle with the same kernel variant bit for
+ * bit.  One material (E, nu) for the whole batch.
+ *
+ * Layout: instance i owns nodes [off_i, off_i + nx_i*ny_i) of the concatenated node
+ * range (off_i = lbm_batch_offset(b, i); lbm_batch_offset(b, count) = total nodes);
+ * population k of its node n at [8 off_i + k N_i + n], two-component fields (force,
+ * target, gradient) at [2 off_i + c N_i + n].  All arrays are device arrays borrowed
+ * for the call; calls are stream-ordered on `stream` and do not synchronise except
+ * create, set_target and tune.  Errors: LBM_ERR_ARG (bad sizes / NULL), LBM_ERR_STATE
+ * (objective or adjoint before set_target, gradient before adjoint), LBM_ERR_OOM,
+ * LBM_ERR_CUDA. */
+typedef struct lbm_batch lbm_batch;
+/* dx: per-instance grid spacing, or NULL for 1/nx_i (unit square).  kernel: LBM_KERNEL_*.
+   Allocates 4 population buffers and 3 two-component fields over the total nodes. */
+lbm_status lbm_batch_create(int count, const int *nx, const int *ny, const double *dx,
+                            double E, double nu, int kernel, void *stream, lbm_batch **out);
+lbm_status lbm_batch_destroy(lbm_batch *b);
+long lbm_batch_offset(const lbm_batch *b, int i); /* node offset of instance i; -1 if bad */
+/* Physical body force of every instance (2 * total values); resets every f_S to 0. */
+lbm_status lbm_batch_set_force(lbm_batch *b, const double *F_dev);
+/* Target displacement of every instance; computes each instance's Cbar (Eq. node_J). */
+lbm_status lbm_batch_set_target(lbm_batch *b, const double *dstar_dev);
+/* `sweeps` collide+stream sweeps of every instance (fixed count, no stopping test). */
+lbm_status lbm_batch_primal(lbm_batch *b, long sweeps);
+/* J of every instance (count values, device) at the current primal state. */
+lbm_status lbm_batch_objective(lbm_batch *b, double *J_dev);
+/* Adjoint from phi_C = 0: `sweeps` iterations of Eq. adjoint_iteration per instance. */
+lbm_status lbm_batch_adjoint(lbm_batch *b, long sweeps);
+/* dJ/dF_n of every instance (2 * total values, device). */
+lbm_status lbm_batch_gradient(lbm_batch *b, double *grad_dev);
+/* which = 0: f_S, 2: phi_C of every instance (8 * total values, device). */
+lbm_status lbm_batch_get_populations(lbm_batch *b, int which, double *dst_dev);
+/* Autotuner: times `sweeps` primal sweeps for tile widths 32, 64, 128 and 256 (tile =
+   width x 256/width nodes), keeps the fastest and restores the primal state.
+   best_bx (may be NULL) receives the chosen width.  Allocates one population-sized
+   scratch buffer for the duration of the call. */
+lbm_status lbm_batch_tune(lbm_batch *b, int sweeps, int *best_bx);
+
+/* ---- Learned warm start ------------------------------------------------------------
+ * The paper has no counterpart: this network only supplies the initial populations of
+ * an iteration (Eq. adjoint_iteration or the primal sweep) that then runs to the same
+ * residual tolerance as from a cold start, so it changes iteration counts, never the
+ * fixed point.  A linear U-Net: `levels` levels of C_l = base * 2^l channels; per level
+ * two 3x3 convolutions with circular padding and bias, 2x2 average pooling between
+ * levels; decoder: nearest 2x upsampling, concatenation [upsampled, skip], two 3x3
+ * convolutions; a 1x1 head to 8 channels.  Input 2 channels, output 8.  BF16 weights
+ * and activations, FP32 accumulation on the tensor cores, FP32 master weights and Adam.
+ *
+ * Layout: x (B, H, W, 2) and y, t (B, H, W, 8) FP32 NHWC device arrays borrowed for
+ * the call; parameters are one FP32 vector, per layer in execution order (encoder
+ * level 0..levels-1: conv a, conv b; decoder level levels-2..0: conv a, conv b; head)
+ * the weights [ky][kx][cin][cout] then the bias [cout].  All calls are stream-ordered
+ * on the create-time stream and return without synchronising, except create and
+ * destroy.  Errors: LBM_ERR_ARG (NULL, base not a positive multiple of 16, levels not
+ * in 1..5, base * 2^(levels-1) > 256, H not divisible by 2^(levels-1), W not divisible
+ * by 16 * 2^(levels-1)), LBM_ERR_OOM, LBM_ERR_CUDA. */
+typedef struct lbm_unet lbm_unet;
+/* Allocates parameters, Adam moments and every activation for batch size `batch` at
+   H x W; weights N(0, 1/fan_in) from `seed`, zero biases. */
+lbm_status lbm_unet_create(int base, int levels, int batch, int H, int W,
+                           unsigned long long seed, void *stream, lbm_unet **out);
+lbm_status lbm_unet_destroy(lbm_unet *u);
+long lbm_unet_param_count(const lbm_unet *u); /* -1 for NULL */
+/* Copies the parameter vector (which = 0) or the last gradient (which = 1) into dst. */
+lbm_status lbm_unet_get_params(lbm_unet *u, float *dst_dev, int which);
+/* Replaces the parameter vector (Adam moments are kept). */
+lbm_status lbm_unet_set_params(lbm_unet *u, const float *src_dev);
+/* y = net(x); y_dev may be NULL (the output then stays internal). */
+lbm_status lbm_unet_forward(lbm_unet *u, const float *x_dev, float *y_dev);
+/* Forward, loss L = (1/2) mean (y - t)^2 into loss_dev (may be NULL), gradient of L
+   w.r.t. every parameter (readable with get_params(which = 1)), then one Adam step
+   (beta 0.9 / 0.999, eps 1e-8) with learning rate lr if lr > 0. */
+lbm_status lbm_unet_train_step(lbm_unet *u, const float *x_dev, const float *t_dev, float lr,
+                               float *loss_dev);
+
+/* Conversions between solver states and the network's tensors, for `count` samples
+ * of one size N = nx * ny laid out like a batch of equal lattices (two-component field
+ * of sample b at [2 b N + c N + n], populations at [8 b N + k N + n]).  The network
+ * sees a resolution-free form of a steady state (Appendix A.1 moments, theta = 1/3):
+ *   mode 1 (primal f_S):  z = (m10, m01, m11/dx, m_s/dx, m_d/dx,
+ *                              (m12 - theta m10)/dx^2, (m21 - theta m01)/dx^2, m22/dx),
+ *     whose sizes do not depend on dx at steady state;
+ *   mode 2 (adjoint phi_C): dx^2 times the same with (1 - theta) for theta (at the
+ *     adjoint fixed point m12 = (1 - theta) m10 and m21 = (1 - theta) m01 exactly, and
+ *     phi grows as 1/dx^2 for a source r = (dx^2/Cbar) w (d - d*));
+ *   mode 0: the plain moments.
+ * Every sample is divided by the RMS s_b of its input field (the states are linear in
+ * it), every channel by a constant c_i (chan_dev, 8 floats, NULL = 1; c_i = 0 marks a
+ * channel that is not predicted: target 0, decoded as 0).  All arrays are device arrays
+ * borrowed for the call; stream-ordered, no synchronisation; no allocation.
+ * LBM_ERR_ARG for bad sizes, mode or NULL, LBM_ERR_CUDA if a launch fails. */
+/* x (count, ny/factor, nx/factor, 2) = factor x factor block means of (field - ref) / s_b,
+   s_b the RMS of field - ref (ref_dev NULL = 0: the state of the field itself; else the
+   state of the change, which is added to the reference's state by decode's accumulate,
+   the states being linear); scale_dev receives s_b (count floats). */
+lbm_status lbm_warm_encode(int count, int nx, int ny, int factor, const double *field_dev,
+                           const double *ref_dev, float *x_dev, float *scale_dev, void *stream);
+/* t (count, ny, nx, 8) = network coordinates of the populations / (s_b c_i); t_dev
+   16-byte aligned. */
+lbm_status lbm_warm_targets(int count, int nx, int ny, double dx, int mode,
+                            const double *pop_dev, const float *scale_dev,
+                            const float *chan_dev, float *t_dev, void *stream);
+/* Populations (count, 8, hc*factor, wc*factor) from network output y (count, hc, wc, 8):
+   periodic bilinear interpolation to the fine nodes (coarse node j = centre of its
+   block), times s_b c_i, moments rescaled with the fine spacing dx_fine, inverted;
+   written to pop_dev, or added to it if accumulate is nonzero. */
+lbm_status lbm_warm_decode(int count, int wc, int hc, int factor, double dx_fine, int mode,
+                           const float *y_dev, const float *scale_dev, const float *chan_dev,
+                           double *pop_dev, int accumulate, void *stream);
+/* rms_i of channel i of an (pixels, 8) tensor over its first min(pixels, 2^22) rows. */
+lbm_status lbm_warm_channel_rms(const float *t_dev, long pixels, float *rms_dev, void *stream);
 
 /* Objective without any device allocation.
  *

@@ -1,0 +1,147 @@
+"""CPU reference of the warm-start network (FP64 numpy) -- TEST INFRASTRUCTURE ONLY.
+
+The learned warm start maps a control field (the 2-component body force on a periodic
+lattice) to the 8 steady post-streaming populations, which the LBM then iterates to the
+requested residual.  The network is a 4-level U-Net:
+
+  level l (l = 0..3) has C_l = base * 2^l channels and two 3x3 convolutions;
+  encoder: conv(2 or C_{l-1} -> C_l), conv(C_l -> C_l), then 2x2 average pooling;
+  decoder: nearest 2x upsampling, concatenation [up, skip_l], conv(C_{l+1} + C_l -> C_l),
+           conv(C_l -> C_l);
+  head: 1x1 convolution C_0 -> 8.
+
+All convolutions use circular padding (the lattice is periodic) and carry a bias; there
+is no nonlinearity: the steady populations are a linear function of the force
+(Section 3.1: the collision is affine in the populations and the force, streaming is a
+permutation), so a linear multi-scale convolution operator is the right model class.
+
+Tensors are (B, H, W, C) float64.  Weights of a 3x3 convolution are (3, 3, Cin, Cout)
+indexed [dy+1, dx+1, ci, co] with out[b, y, x, co] = bias[co] +
+sum_{dy,dx,ci} in[b, (y+dy) mod H, (x+dx) mod W, ci] w[dy+1, dx+1, ci, co].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def layer_shapes(base: int = 32, cin: int = 2, cout: int = 8, levels: int = 4):
+    """[(name, kernel, cin, cout)] in execution order."""
+    ch = [base * 2 ** l for l in range(levels)]
+    shapes = []
+    c = cin
+    for l in range(levels):
+        shapes.append(("enc%d_a" % l, 3, c, ch[l]))
+        shapes.append(("enc%d_b" % l, 3, ch[l], ch[l]))
+        c = ch[l]
+    for l in range(levels - 2, -1, -1):
+        shapes.append(("dec%d_a" % l, 3, ch[l + 1] + ch[l], ch[l]))
+        shapes.append(("dec%d_b" % l, 3, ch[l], ch[l]))
+    shapes.append(("head", 1, ch[0], cout))
+    return shapes
+
+
+def init_params(shapes, seed: int = 0):
+    """He-style scaled normal weights (fan-in), zero biases."""
+    rng = np.random.default_rng(seed)
+    params = {}
+    for name, k, ci, co in shapes:
+        params[name + ".w"] = rng.standard_normal((k, k, ci, co)) * np.sqrt(1.0 / (k * k * ci))
+        params[name + ".b"] = np.zeros(co)
+    return params
+
+
+def conv(x, w, b):
+    k = w.shape[0]
+    out = np.zeros(x.shape[:3] + (w.shape[3],)) + b
+    r = k // 2
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            xs = np.roll(x, shift=(-dy, -dx), axis=(1, 2))  # xs[y, x] = x[y+dy, x+dx]
+            out += xs @ w[dy + r, dx + r]
+    return out
+
+
+def conv_backward(x, w, gout):
+    """(grad_x, grad_w, grad_b) of conv for upstream gradient gout."""
+    k = w.shape[0]
+    r = k // 2
+    gx = np.zeros_like(x)
+    gw = np.zeros_like(w)
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            xs = np.roll(x, shift=(-dy, -dx), axis=(1, 2))
+            gw[dy + r, dx + r] = np.einsum("bhwc,bhwd->cd", xs, gout)
+            gx += np.roll(gout @ w[dy + r, dx + r].T, shift=(dy, dx), axis=(1, 2))
+    gb = gout.sum(axis=(0, 1, 2))
+    return gx, gw, gb
+
+
+def pool(x):
+    B, H, W, C = x.shape
+    return x.reshape(B, H // 2, 2, W // 2, 2, C).mean(axis=(2, 4))
+
+
+def pool_backward(g):
+    return np.repeat(np.repeat(g, 2, axis=1), 2, axis=2) * 0.25
+
+
+def up(x):
+    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+
+
+def up_backward(g):
+    B, H, W, C = g.shape
+    return g.reshape(B, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
+
+
+def forward(params, x, levels: int = 4, keep: bool = False):
+    """Network output (B, H, W, 8); with keep, also the activations for backward."""
+    acts = {}
+    skips = []
+    h = x
+    for l in range(levels):
+        acts["enc%d_a" % l] = h
+        h = conv(h, params["enc%d_a.w" % l], params["enc%d_a.b" % l])
+        acts["enc%d_b" % l] = h
+        h = conv(h, params["enc%d_b.w" % l], params["enc%d_b.b" % l])
+        if l < levels - 1:
+            skips.append(h)
+            h = pool(h)
+    for l in range(levels - 2, -1, -1):
+        h = np.concatenate([up(h), skips[l]], axis=3)
+        acts["dec%d_a" % l] = h
+        h = conv(h, params["dec%d_a.w" % l], params["dec%d_a.b" % l])
+        acts["dec%d_b" % l] = h
+        h = conv(h, params["dec%d_b.w" % l], params["dec%d_b.b" % l])
+    acts["head"] = h
+    y = conv(h, params["head.w"], params["head.b"])
+    return (y, acts) if keep else y
+
+
+def backward(params, acts, gy, levels: int = 4):
+    """Gradients of a scalar loss with upstream gradient gy w.r.t. every parameter."""
+    grads = {}
+    g, grads["head.w"], grads["head.b"] = conv_backward(acts["head"], params["head.w"], gy)
+    skip_grads = {}
+    for l in range(0, levels - 1):  # decoder in reverse execution order: level 0 first
+        g, grads["dec%d_b.w" % l], grads["dec%d_b.b" % l] = conv_backward(
+            acts["dec%d_b" % l], params["dec%d_b.w" % l], g)
+        g, grads["dec%d_a.w" % l], grads["dec%d_a.b" % l] = conv_backward(
+            acts["dec%d_a" % l], params["dec%d_a.w" % l], g)
+        cu = params["dec%d_a.w" % l].shape[2] - params["dec%d_b.w" % l].shape[2]
+        skip_grads[l] = g[..., cu:]
+        g = up_backward(g[..., :cu])
+    for l in range(levels - 1, -1, -1):
+        if l < levels - 1:
+            g = pool_backward(g) + skip_grads[l]
+        g, grads["enc%d_b.w" % l], grads["enc%d_b.b" % l] = conv_backward(
+            acts["enc%d_b" % l], params["enc%d_b.w" % l], g)
+        g, grads["enc%d_a.w" % l], grads["enc%d_a.b" % l] = conv_backward(
+            acts["enc%d_a" % l], params["enc%d_a.w" % l], g)
+    return grads
+
+
+def mse_loss(y, t):
+    """0.5 * mean((y - t)^2) and its gradient."""
+    d = y - t
+    return 0.5 * float(np.mean(d * d)), d / d.size

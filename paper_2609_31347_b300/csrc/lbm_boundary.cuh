@@ -116,7 +116,7 @@ __device__ inline Material material_of(double E, double nu) {
 // with respect to E (dQ, ds; skipped when dQ == nullptr).  With a modulus field
 // (alpha != nullptr) each record takes the material of its own node and also stores
 // its boundary gamma (Eq. gamma with tau_f = 1/2).
-__global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, long nb, Material m0,
+static __global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, long nb, Material m0,
                                  double dx, double *__restrict__ Q, double *__restrict__ s,
                                  double *__restrict__ dQ, double *__restrict__ ds,
                                  const double *__restrict__ alpha, const int *__restrict__ bnode,

@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) k_grad_young(const double *__restrict__ f
 
 // Per-node collision constants of a modulus field: E_n = alpha_n^2 (Eq. E_substitution),
 // plane-stress moduli (Eqs. mu, K), relaxation (Table A.1, Eq. relaxation).
-__global__ void k_set_young_field(const double *__restrict__ alpha, double nu, long N,
+static __global__ void k_set_young_field(const double *__restrict__ alpha, double nu, long N,
                                   double *__restrict__ q) {
   for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N;
        n += (long)gridDim.x * blockDim.x) {
@@ -483,6 +483,131 @@ __global__ void k_set_young_field(const double *__restrict__ alpha, double nu, l
     q[N + n] = 0.25 * (1.0 - ws);
     q[2 * N + n] = 0.25 * (1.0 - wd);
   }
+}
+
+// Tangent of the streaming step at (x, y): tf_S = S' tf_C + Edot (dS'/dE f_C + ds/dE),
+// i.e. the boundary rules without their constant part, plus their E-derivative applied
+// to the primal post-collision state fprim.  Returns false for outside nodes; bnd tells
+// whether the node is a boundary node.
+template <bool BOUNDED, bool YOUNG>
+__device__ __forceinline__ bool pull_tangent(const double *__restrict__ tin,
+                                             const double *__restrict__ fprim, int x, int y,
+                                             const Grid &g, const Bounded &b, double Edot,
+                                             double (&t)[8], bool &bnd) {
+  const long n = (long)y * g.nx + x;
+  double gsel;
+  bnd = false;
+  if (!BOUNDED) return pull_primal<false>(tin, x, y, g, b, t, gsel);
+  const uint8_t ty = b.type[n];
+  if (ty == 0) return false;
+  if (ty == 1) return pull_primal<true>(tin, x, y, g, b, t, gsel);
+  bnd = true;
+  const int bi = b.bidx[n];
+  const unsigned reg = b.regmask[bi];
+  double own[8], ownf[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    own[j] = tin[j * g.N + n];
+    ownf[j] = YOUNG ? fprim[j * g.N + n] : 0.0;
+  }
+  for (int k = 0; k < 8; ++k) {
+    if (reg & (1u << k)) {
+      t[k] = tin[k * g.N + n - kCX[k] - (long)kCY[k] * g.nx];
+    } else {
+      double acc = 0.0, dacc = YOUNG ? b.ds[(long)bi * 8 + k] : 0.0;
+      for (int j = 0; j < 8; ++j) {
+        acc += b.Q[(long)bi * 64 + k * 8 + j] * own[j];
+        if (YOUNG) dacc += b.dQ[(long)bi * 64 + k * 8 + j] * ownf[j];
+      }
+      t[k] = acc + (YOUNG ? Edot * dacc : 0.0);
+    }
+  }
+  return true;
+}
+
+// Forward-mode (f-AD, Eq. fAD) tangent sweep at a converged primal state (held in fprim
+// as f_C, so that f_S = S' f_C + s): the tangent obeys the differentiated step
+//   tf_S = S' tf_C + Edot (dS'/dE f_C + ds/dE),
+//   tf_C = A tf_S + B tg + Edot (dC/dE) f_S,
+// with tg = dx^2 dF (the force direction, kept as q-dot = tg / 4) and Edot the modulus
+// direction.  dC/dE uses the same pair-form derivatives as k_grad_young.
+template <bool BOUNDED, bool YOUNG>
+__global__ void __launch_bounds__(256) k_tangent(const double *__restrict__ fprim,
+                                                 const double *__restrict__ tin,
+                                                 double *__restrict__ tout,
+                                                 const double *__restrict__ qdot, Grid g,
+                                                 Bounded b, Coef c, YoungDeriv yd, double Edot) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const long n = (long)y * g.nx + x;
+  double t[8];
+  bool bnd;
+  if (!pull_tangent<BOUNDED, YOUNG>(tin, fprim, x, y, g, b, Edot, t, bnd)) return;
+  double o[8], dd, de;
+  const double qx = qdot ? qdot[n] : 0.0, qy = qdot ? qdot[g.N + n] : 0.0;
+  if (bnd)
+    collide<true>(t, qx, qy, c, o, dd, de);
+  else
+    collide<false>(t, qx, qy, c, o, dd, de);
+  if (YOUNG) {
+    double f[8], gs2;
+    pull_primal<BOUNDED>(fprim, x, y, g, b, f, gs2);
+    const double m11 = (f[4] + f[6]) - (f[5] + f[7]);
+    const double ms = (f[0] + f[1] + f[2] + f[3]) + 2.0 * (f[4] + f[5] + f[6] + f[7]);
+    const double md = (f[0] + f[2]) - (f[1] + f[3]);
+    const double gam = bnd ? c.gam : 0.0;
+    const double d11 = Edot * yd.dc11 * 0.25 * m11;
+    const double dd_ = Edot * yd.dcd * 0.25 * md;
+    double dax = Edot * yd.dcs * ms * (0.25 + 0.5 * gam);
+    double ddg = -Edot * yd.dcs * ms * 0.25 * gam;
+    if (bnd) {
+      dax += Edot * yd.dgam * c.cs * ms * 0.5;
+      ddg -= Edot * yd.dgam * c.cs * ms * 0.25;
+    }
+    o[0] += dax + dd_;
+    o[2] += dax + dd_;
+    o[1] += dax - dd_;
+    o[3] += dax - dd_;
+    o[4] += ddg + d11;
+    o[6] += ddg + d11;
+    o[5] += ddg - d11;
+    o[7] += ddg - d11;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) tout[k * g.N + n] = o[k];
+}
+
+// dJ along the tangent: sum_n obs (d - d*) . d-dot, with d from the primal state and
+// d-dot = m10(tf_S) + 2 q-dot (times dx^2 / Cbar outside).
+template <bool BOUNDED, bool YOUNG>
+__global__ void __launch_bounds__(256) k_tangent_objective(
+    const double *__restrict__ fprim, const double *__restrict__ tcur,
+    const double *__restrict__ g2, const double *__restrict__ qdot,
+    const double *__restrict__ dstar, const double *__restrict__ obs, Grid g, Bounded b,
+    double Edot, double *__restrict__ partial) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  double acc[1] = {0.0};
+  if (x < g.nx && y < g.ny) {
+    const long n = (long)y * g.nx + x;
+    double f[8], t[8], gs;
+    bool bnd;
+    if (pull_primal<BOUNDED>(fprim, x, y, g, b, f, gs) &&
+        pull_tangent<BOUNDED, YOUNG>(tcur, fprim, x, y, g, b, Edot, t, bnd)) {
+      const double w = obs ? obs[n] : 1.0;
+      const double ex = (f[0] - f[2]) + (f[4] - f[6]) - (f[5] - f[7]) + 2.0 * g2[n] - dstar[n];
+      const double ey = (f[1] - f[3]) + (f[4] - f[6]) + (f[5] - f[7]) + 2.0 * g2[g.N + n] -
+                        dstar[g.N + n];
+      const double tx = (t[0] - t[2]) + (t[4] - t[6]) - (t[5] - t[7]) + (qdot ? 2.0 * qdot[n] : 0.0);
+      const double ty = (t[1] - t[3]) + (t[4] - t[6]) + (t[5] - t[7]) +
+                        (qdot ? 2.0 * qdot[g.N + n] : 0.0);
+      acc[0] = w * (ex * tx + ey * ty);
+    }
+  }
+  __shared__ double sm[32];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
 }
 
 // Subtract per-component means over active nodes (Eq. zero_mean_projection).
@@ -499,7 +624,7 @@ __global__ void k_subtract_mean(double *__restrict__ v, const double *__restrict
 }
 
 // Residual partials: max |a - b| and max |a| over all planes.
-__global__ void __launch_bounds__(256) k_residual(const double *__restrict__ a,
+static __global__ void __launch_bounds__(256) k_residual(const double *__restrict__ a,
                                                   const double *__restrict__ bb, long total,
                                                   double *__restrict__ partial) {
   double v[2] = {0.0, 0.0};
@@ -518,7 +643,7 @@ __global__ void __launch_bounds__(256) k_residual(const double *__restrict__ a,
 }
 
 // Second pass: out[v] = reduce over nb partials (fixed order, one block).  op 0 sum, 1 max.
-__global__ void __launch_bounds__(256) k_finish(const double *__restrict__ partial, long nb,
+static __global__ void __launch_bounds__(256) k_finish(const double *__restrict__ partial, long nb,
                                                 int nv, int op, double scale,
                                                 double *__restrict__ out) {
   __shared__ double sm[32 * 4];
@@ -539,7 +664,7 @@ __global__ void __launch_bounds__(256) k_finish(const double *__restrict__ parti
 
 // Quarter lattice force q = g / 4 = dx^2 (a1 Phi_1 + a2 Phi_2) / 4 from the two basis
 // fields, or q = dx^2 F / 4 from a nodal force (alpha == nullptr).
-__global__ void k_set_force(double *__restrict__ g2, const double *__restrict__ src,
+static __global__ void k_set_force(double *__restrict__ g2, const double *__restrict__ src,
                             const double *__restrict__ basis, const double *__restrict__ alpha2,
                             double dx2, long N, const uint8_t *__restrict__ type) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 2 * N;

@@ -56,6 +56,8 @@ struct lbm_solid {
   };
   std::vector<GraphEnt> graphs;
   long version = 0;
+  // forward-mode tangent (f-AD) buffers, allocated on first use
+  double *tA = nullptr, *tB = nullptr, *qdot = nullptr;
   BoundaryNode *bnodes = nullptr;
   long nb = 0;
   double *partial = nullptr;
@@ -458,7 +460,8 @@ lbm_status objective_partials(lbm_solid *h) {
 void free_all(lbm_solid *h) {
   void *bufs[] = {h->fA, h->fB, h->pA, h->pB, h->g2, h->r2, h->dstar, h->obs, h->basis, h->Fbase,
                   h->type, h->regmask, h->bidx, h->Q, h->s, h->dQ, h->ds, h->bnodes,
-                  h->partial, h->dres, h->qfield, h->alphaN, h->gamf, h->bnode};
+                  h->partial, h->dres, h->qfield, h->alphaN, h->gamf, h->bnode, h->tA, h->tB,
+                  h->qdot};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (h->hres) cudaFreeHost(h->hres);
@@ -790,6 +793,17 @@ lbm_status lbm_solid_objective(lbm_solid *h, double *J) {
   return LBM_OK;
 }
 
+lbm_status lbm_solid_adjoint_source(lbm_solid *h, double *r) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!r) return fail(h, LBM_ERR_ARG, "r is NULL");
+  if (!h->have_target) return fail(h, LBM_ERR_STATE, "adjoint_source needs set_target first");
+  lbm_status st = objective_partials(h);
+  if (st) return st;
+  CK(h, cudaMemcpyAsync(r, h->r2, sizeof(double) * 2 * h->N, cudaMemcpyDeviceToDevice, h->stream));
+  return LBM_OK;
+}
+
 lbm_status lbm_solid_adjoint_solve(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *info) {
   if (!h) return LBM_ERR_ARG;
   if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
@@ -861,6 +875,102 @@ lbm_status lbm_solid_gradient(lbm_solid *h, double *grad, size_t n, int project)
     return LBM_OK;
   }
   return fail(h, LBM_ERR_ARG, "gradient for this control kind is not built");
+}
+
+lbm_status lbm_solid_tangent(lbm_solid *h, const double *seed, size_t n,
+                             const lbm_solve_opts *o, double *dJ, lbm_solve_info *info) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->broken) return fail(h, LBM_ERR_CUDA, "handle unusable after a CUDA error");
+  if (!seed || !dJ) return fail(h, LBM_ERR_ARG, "seed or dJ is NULL");
+  lbm_status st = check_opts(h, o);
+  if (st) return st;
+  if (!h->have_target) return fail(h, LBM_ERR_STATE, "tangent needs set_target first");
+  if (h->fcur_is_fs) return fail(h, LBM_ERR_STATE, "tangent needs a primal solve");
+  const long N = h->N;
+  const size_t pop = sizeof(double) * 8 * N;
+  if (!h->tA) {
+    CK(h, cudaMalloc(&h->tA, pop));
+    CK(h, cudaMalloc(&h->tB, pop));
+    CK(h, cudaMalloc(&h->qdot, sizeof(double) * 2 * N));
+  }
+  const uint8_t *tp = h->periodic ? nullptr : h->type;
+  const double q4 = 0.25 * h->dx * h->dx;
+  bool young = false;
+  double Edot = 0.0;
+  if (h->control == LBM_CTRL_FORCE_FIELD) {
+    if (n != (size_t)(2 * N)) return fail(h, LBM_ERR_ARG, "FORCE_FIELD seed has 2N values");
+    k_set_force<<<148 * 4, 256, 0, h->stream>>>(h->qdot, seed, nullptr, nullptr, q4, N, tp);
+    LAUNCHED(h);
+  } else if (h->control == LBM_CTRL_FORCE_BASIS2) {
+    if (n != 2) return fail(h, LBM_ERR_ARG, "FORCE_BASIS2 seed has 2 values");
+    k_set_force<<<148 * 4, 256, 0, h->stream>>>(h->qdot, nullptr, h->basis, seed, q4, N, tp);
+    LAUNCHED(h);
+  } else if (h->control == LBM_CTRL_YOUNG_SCALAR) {
+    if (n != 1) return fail(h, LBM_ERR_ARG, "YOUNG_SCALAR seed has 1 value");
+    CK(h, cudaMemcpyAsync(h->hres, seed, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    young = true;
+    Edot = 2.0 * h->alpha * h->hres[0];  // E = alpha^2
+  } else {
+    return fail(h, LBM_ERR_ARG, "tangent is built for force controls and the scalar modulus");
+  }
+  const double *qd = young ? nullptr : h->qdot;
+  // both buffers: the sweep never writes inactive nodes, which the residual still reads
+  CK(h, cudaMemsetAsync(h->tA, 0, pop, h->stream));
+  CK(h, cudaMemsetAsync(h->tB, 0, pop, h->stream));
+  double *tcur = h->tA, *tnext = h->tB;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto sweep = [&]() -> lbm_status {
+    if (h->periodic) {
+      if (young) k_tangent<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, tnext, qd, h->grid, h->bnd, h->coef, h->yd, Edot);
+      else k_tangent<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, tnext, qd, h->grid, h->bnd, h->coef, h->yd, Edot);
+    } else {
+      if (young) k_tangent<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, tnext, qd, h->grid, h->bnd, h->coef, h->yd, Edot);
+      else k_tangent<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, tnext, qd, h->grid, h->bnd, h->coef, h->yd, Edot);
+    }
+    LAUNCHED(h);
+    std::swap(tcur, tnext);
+    return LBM_OK;
+  };
+  long steps = 0;
+  double metric = 0.0;
+  lbm_status result = LBM_OK;
+  if (o->fixed_steps) {
+    for (; steps < o->max_steps; ++steps)
+      if ((st = sweep())) return st;
+  } else {
+    bool done = false;
+    while (!done && steps < o->max_steps) {
+      long k = o->check_every < o->max_steps - steps ? o->check_every : o->max_steps - steps;
+      for (long i = 0; i < k; ++i)
+        if ((st = sweep())) return st;
+      steps += k;
+      if (steps < 2) continue;
+      if ((st = residual(h, tcur, tnext, metric))) return st;
+      if (std::isnan(metric)) { result = LBM_ERR_DIVERGED; break; }
+      if (metric < o->tol) done = true;
+    }
+    if (result == LBM_OK && !done) result = LBM_ERR_NOT_CONVERGED;
+  }
+  if (h->periodic) {
+    if (young) k_tangent_objective<false, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, h->g2, qd, h->dstar, h->obs, h->grid, h->bnd, Edot, h->partial);
+    else k_tangent_objective<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, h->g2, qd, h->dstar, h->obs, h->grid, h->bnd, Edot, h->partial);
+  } else {
+    if (young) k_tangent_objective<true, true><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, h->g2, qd, h->dstar, h->obs, h->grid, h->bnd, Edot, h->partial);
+    else k_tangent_objective<true, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, tcur, h->g2, qd, h->dstar, h->obs, h->grid, h->bnd, Edot, h->partial);
+  }
+  LAUNCHED(h);
+  if ((st = finish(h, h->nblocks2d, 1, 0, h->dx * h->dx / h->cbar, h->dres))) return st;
+  if ((st = fetch(h, 1))) return st;
+  *dJ = h->hres[0];
+  if (info) {
+    info->steps = steps;
+    info->last_metric = metric;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (result == LBM_ERR_NOT_CONVERGED) h->err = "max_steps reached before the stopping rule held";
+  if (result == LBM_ERR_DIVERGED) h->err = "non-finite tangent residual";
+  return result;
 }
 
 lbm_status lbm_solid_get_populations(lbm_solid *h, int which, double *dst) {

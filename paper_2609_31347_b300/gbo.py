@@ -41,11 +41,17 @@ class LBMObjective(torch.autograd.Function):
     """J(alpha) with dJ/dalpha from the discrete adjoint."""
 
     @staticmethod
-    def forward(ctx, alpha, solver, primal: SolveOpts, adjoint: SolveOpts, project: bool):
-        solver.set_control(alpha.detach().contiguous())
+    def forward(ctx, alpha, solver, primal: SolveOpts, adjoint: SolveOpts, project: bool,
+                warm=None):
+        a = alpha.detach().contiguous()
+        solver.set_control(a)
+        if warm is not None:
+            warm.before_primal(solver, a)
         solver.primal_solve(**primal.kw())
+        if warm is not None:
+            warm.after_primal(solver, a)
         J = solver.objective()
-        ctx.solver, ctx.adjoint, ctx.project = solver, adjoint, project
+        ctx.solver, ctx.adjoint, ctx.project, ctx.warm = solver, adjoint, project, warm
         ctx.fS = solver.get_populations(0).clone()  # steady-state checkpoint
         ctx.alpha = alpha.detach().clone()
         solver._state_token = id(ctx)
@@ -61,15 +67,21 @@ class LBMObjective(torch.autograd.Function):
             s.set_populations(0, ctx.fS)
             s.primal_solve(1, fixed_steps=True)
             s._state_token = ctx.token
+        if ctx.warm is not None:
+            ctx.warm.before_adjoint(s)
         s.adjoint_solve(**ctx.adjoint.kw())
+        if ctx.warm is not None:
+            ctx.warm.after_adjoint(s)
         g = s.gradient(project_zero_mean=ctx.project)
-        return gJ * g.view_as(ctx.alpha), None, None, None, None
+        return gJ * g.view_as(ctx.alpha), None, None, None, None, None
 
 
 def objective(alpha, solver, primal: Optional[SolveOpts] = None,
-              adjoint: Optional[SolveOpts] = None, project: bool = False):
+              adjoint: Optional[SolveOpts] = None, project: bool = False, warm=None):
+    """J(alpha) as a differentiable torch scalar.  warm: optional initial-state supplier
+    (``warmstart.WarmStarter``) for the primal and adjoint solves."""
     return LBMObjective.apply(alpha, solver, primal or SolveOpts(), adjoint or SolveOpts(),
-                              project)
+                              project, warm)
 
 
 @dataclass
@@ -212,11 +224,11 @@ def lbfgs(fg: Callable, alpha0: torch.Tensor, m_max: int = 50, eps: float = 1e-1
 
 
 def make_fg(solver, primal: Optional[SolveOpts] = None, adjoint: Optional[SolveOpts] = None,
-            project: bool = False):
+            project: bool = False, warm=None):
     """(J, grad) closure for lbfgs through the autograd function."""
     def fg(a):
         a = a.detach().clone().requires_grad_(True)
-        J = objective(a, solver, primal, adjoint, project)
+        J = objective(a, solver, primal, adjoint, project, warm)
         J.backward()
         return float(J.detach()), a.grad.detach().clone()
     return fg

@@ -123,6 +123,37 @@ def fourier_force(nx: int, modes: int = 8, kmax: int = 4, seed: int = 1, ny: Opt
     return F.reshape(2, nx * ny)
 
 
+def fourier_fields(count: int, nx: int, seed: int, modes: int = 8, kmax: int = 8,
+                   unit_norm: bool = False, device: str = "cuda"):
+    """`count` random zero-mean two-component fields on the periodic nx^2 grid, as a
+    (count, 2, nx*nx) float64 torch tensor on `device` (the layout of a batch of equal
+    lattices).  Each field is `modes` Fourier modes with wavevectors 2 pi (kx, ky),
+    kx, ky in {-kmax..kmax} not both zero, and N(0, 1/|k|^2) sin/cos amplitudes per
+    component (smoother fields have more weight, as do the steady states they drive).
+    unit_norm scales every field to Euclidean norm 1 over its 2N values."""
+    import torch
+    rng = np.random.default_rng(seed)
+    k = rng.integers(-kmax, kmax + 1, size=(count, modes, 2))
+    zero = (k[..., 0] == 0) & (k[..., 1] == 0)
+    k[zero, 0] = 1
+    amp = rng.standard_normal((count, modes, 4)) / np.hypot(k[..., 0], k[..., 1])[..., None]
+    x = torch.arange(nx, dtype=torch.float64, device=device) / nx
+    Y, X = torch.meshgrid(x, x, indexing="ij")
+    kt = torch.as_tensor(k, dtype=torch.float64, device=device)
+    at = torch.as_tensor(amp, dtype=torch.float64, device=device)
+    out = torch.empty((count, 2, nx * nx), dtype=torch.float64, device=device)
+    for b in range(count):
+        ph = TWO_PI * (kt[b, :, 0, None, None] * X + kt[b, :, 1, None, None] * Y)  # (modes, nx, nx)
+        s, c = torch.sin(ph), torch.cos(ph)
+        a = at[b]
+        out[b, 0] = (a[:, 0, None, None] * s + a[:, 1, None, None] * c).sum(0).reshape(-1)
+        out[b, 1] = (a[:, 2, None, None] * s + a[:, 3, None, None] * c).sum(0).reshape(-1)
+    out -= out.mean(dim=2, keepdim=True)
+    if unit_norm:
+        out /= torch.linalg.vector_norm(out, dim=(1, 2), keepdim=True)
+    return out
+
+
 def random_state(n: int, seed: int, scale: float = 1.0):
     """Random populations / adjoint states (8, n), N(0, scale^2)."""
     return np.random.default_rng(seed).standard_normal((8, n)) * scale
@@ -191,6 +222,7 @@ class PlateGeometry:
     link: np.ndarray        # (8, N) uint8: 0 regular, 1 Dirichlet-missing, 2 Neumann-missing
     node_type: np.ndarray   # (N,) uint8: 0 outside, 1 interior, 2 boundary
     normal: np.ndarray      # (2, N) outward unit normal of the outer ellipse (boundary nodes)
+    normal_hole: Optional[np.ndarray] = None  # (2, N) normal into the nearest hole (out of Omega^E)
 
 
 def plate_geometry(Nx: int, ellipses=PLATE_ELLIPSES, box: float = 1.5) -> PlateGeometry:
@@ -227,15 +259,30 @@ def plate_geometry(Nx: int, ellipses=PLATE_ELLIPSES, box: float = 1.5) -> PlateG
     gn = np.sqrt(gx * gx + gy * gy)
     gn[gn == 0] = 1.0
     normal = np.vstack([gx / gn, gy / gn])
-    return PlateGeometry(nx, dx, X, Y, active, link, node_type, normal)
+    # normal into the nearest inner ellipse (the outward normal of Omega^E at the holes)
+    hl, hx, hy = lev[1]
+    for (l2, gx2, gy2) in lev[2:]:
+        m = l2 < hl
+        hl, hx, hy = np.where(m, l2, hl), np.where(m, gx2, hx), np.where(m, gy2, hy)
+    hn = np.sqrt(hx * hx + hy * hy)
+    hn[hn == 0] = 1.0
+    normal_hole = np.vstack([-hx / hn, -hy / hn])
+    return PlateGeometry(nx, dx, X, Y, active, link, node_type, normal, normal_hole)
 
 
-def plate_wall_data(geo: PlateGeometry, dstar, sigma):
-    """Per-node wall data: Dirichlet displacement d_D = d*(x_n); Neumann traction
-    T = sigma*(x_n) n(x_n) with n the outer ellipse's outward normal."""
-    T = np.vstack([sigma[0] * geo.normal[0] + sigma[2] * geo.normal[1],
-                   sigma[2] * geo.normal[0] + sigma[1] * geo.normal[1]])
-    return dstar.copy(), T
+def plate_wall_data(geo: PlateGeometry, E=PLATE_E, nu=PLATE_NU, delta=PAPER_DELTA):
+    """Per-node wall data of the manufactured solution, evaluated where the halfway-wall
+    boundary rules place the wall: half a cell outward from the node along the outward
+    normal of Omega^E.  Dirichlet: d_D = d*(x_n + dx/2 n_hole); Neumann:
+    T = sigma*(x_n + dx/2 n) n with n the outer ellipse's outward normal."""
+    h = 0.5 * geo.dx
+    nh = geo.normal_hole
+    dD, _, _ = plate_manufactured(geo.X + h * nh[0], geo.Y + h * nh[1], E=E, nu=nu, delta=delta)
+    _, sN, _ = plate_manufactured(geo.X + h * geo.normal[0], geo.Y + h * geo.normal[1], E=E,
+                                  nu=nu, delta=delta)
+    T = np.vstack([sN[0] * geo.normal[0] + sN[2] * geo.normal[1],
+                   sN[2] * geo.normal[0] + sN[1] * geo.normal[1]])
+    return dD, T
 
 
 def baseline_plate(Nx: int, traction: float = 0.01):

@@ -30,6 +30,12 @@ EXPORTED = [
     "lbm_solid_gradient", "lbm_solid_get_populations", "lbm_solid_set_populations",
     "lbm_solid_displacement", "lbm_solid_launch_count", "lbm_status_string",
     "lbm_solid_last_error", "lbm_objective_noalloc",
+    "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_offset", "lbm_batch_set_force",
+    "lbm_batch_set_target", "lbm_batch_primal", "lbm_batch_objective", "lbm_batch_adjoint",
+    "lbm_batch_gradient", "lbm_batch_get_populations", "lbm_batch_tune", "lbm_solid_tangent",
+    "lbm_unet_create", "lbm_unet_destroy", "lbm_unet_param_count", "lbm_unet_get_params",
+    "lbm_unet_set_params", "lbm_unet_forward", "lbm_unet_train_step",
+    "lbm_solid_adjoint_source", "lbm_warm_encode", "lbm_warm_targets", "lbm_warm_decode", "lbm_warm_channel_rms",
 ]
 
 
@@ -89,6 +95,31 @@ def load_library(path: str = LIB_PATH):
         "lbm_status_string": ([I], ctypes.c_char_p),
         "lbm_solid_last_error": ([P], ctypes.c_char_p),
         "lbm_objective_noalloc": ([I, I, D, P, P, P, P, P, P], I),
+        "lbm_batch_create": ([I, P, P, P, D, D, I, P, ctypes.POINTER(P)], I),
+        "lbm_batch_destroy": ([P], I),
+        "lbm_batch_offset": ([P, I], ctypes.c_long),
+        "lbm_batch_set_force": ([P, P], I),
+        "lbm_batch_set_target": ([P, P], I),
+        "lbm_batch_primal": ([P, ctypes.c_long], I),
+        "lbm_batch_objective": ([P, P], I),
+        "lbm_batch_adjoint": ([P, ctypes.c_long], I),
+        "lbm_batch_gradient": ([P, P], I),
+        "lbm_batch_get_populations": ([P, I, P], I),
+        "lbm_batch_tune": ([P, I, ctypes.POINTER(I)], I),
+        "lbm_solid_tangent": ([P, P, S, ctypes.POINTER(_Opts), ctypes.POINTER(D),
+                               ctypes.POINTER(_Info)], I),
+        "lbm_unet_create": ([I, I, I, I, I, ctypes.c_ulonglong, P, ctypes.POINTER(P)], I),
+        "lbm_unet_destroy": ([P], I),
+        "lbm_unet_param_count": ([P], ctypes.c_long),
+        "lbm_unet_get_params": ([P, P, I], I),
+        "lbm_unet_set_params": ([P, P], I),
+        "lbm_unet_forward": ([P, P, P], I),
+        "lbm_unet_train_step": ([P, P, P, ctypes.c_float, P], I),
+        "lbm_solid_adjoint_source": ([P, P], I),
+        "lbm_warm_encode": ([I, I, I, I, P, P, P, P, P], I),
+        "lbm_warm_targets": ([I, I, I, D, I, P, P, P, P, P], I),
+        "lbm_warm_decode": ([I, I, I, I, D, I, P, P, P, P, I, P], I),
+        "lbm_warm_channel_rms": ([P, ctypes.c_long, P, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -115,10 +146,11 @@ def _host(a, dtype, n=None):
     return a
 
 
-def _dev_ptr(t, n=None):
+def _dev_ptr(t, n=None, dtype=None):
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
-        raise TypeError("expected a CUDA float64 tensor")
+    dtype = torch.float64 if dtype is None else dtype
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype):
+        raise TypeError("expected a CUDA %s tensor" % dtype)
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     if n is not None and t.numel() != n:
@@ -136,6 +168,7 @@ class LBMSolid:
         import torch
         self._lib = load_library()
         self.nx, self.ny, self.N = int(nx), int(ny), int(nx) * int(ny)
+        self.sweeps = {}  # sweeps performed per solve kind ("primal_solve", ...)
         self.control = control
         N = self.N
         keep = [_host(node_mask, np.uint8, N), _host(link_bc, np.uint8, 8 * N),
@@ -196,6 +229,7 @@ class LBMSolid:
         o = self._opts(max_steps, tol, criterion, window, check_every, fixed_steps)
         info = _Info()
         st = fn(self._h, ctypes.byref(o), ctypes.byref(info))
+        self.sweeps[what] = self.sweeps.get(what, 0) + int(info.steps)
         if st != LBM_OK and not (allow_not_converged and
                                  st in (LBM_ERR_NOT_CONVERGED, LBM_ERR_DIVERGED)):
             self._check(st, what)
@@ -213,10 +247,29 @@ class LBMSolid:
         return self._solve(self._lib.lbm_solid_adjoint_solve, "adjoint_solve", max_steps, tol,
                            criterion, window, check_every, fixed_steps, allow_not_converged)
 
+    def tangent(self, seed, max_steps: int = 2_000_000, tol: float = 1e-12,
+                check_every: int = 64, fixed_steps: bool = False) -> float:
+        """Forward-mode dJ along `seed` (device tensor) at the current primal state."""
+        o = self._opts(max_steps, tol, 1, 2, check_every, fixed_steps)
+        dJ, info = ctypes.c_double(), _Info()
+        st = self._lib.lbm_solid_tangent(self._h, _dev_ptr(seed), seed.numel(), ctypes.byref(o),
+                                         ctypes.byref(dJ), ctypes.byref(info))
+        self._check(st, "tangent")
+        return dJ.value
+
     def objective(self) -> float:
         J = ctypes.c_double()
         self._check(self._lib.lbm_solid_objective(self._h, ctypes.byref(J)), "objective")
         return J.value
+
+    def adjoint_source(self, out=None):
+        """r = (dx^2/Cbar) w (d - d*) of the current primal state (2N, device)."""
+        import torch
+        if out is None:
+            out = torch.empty(2 * self.N, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lbm_solid_adjoint_source(self._h, _dev_ptr(out, 2 * self.N)),
+                    "adjoint_source")
+        return out
 
     def gradient(self, out=None, project_zero_mean: bool = False):
         import torch
@@ -249,3 +302,165 @@ class LBMSolid:
         self._check(self._lib.lbm_solid_displacement(self._h, _dev_ptr(out, 2 * self.N)),
                     "displacement")
         return out
+
+
+class LBMBatch:
+    """Many periodic lattices of uneven size advanced together (one launch per sweep)."""
+
+    def __init__(self, sizes, E: float, nu: float, dx=None, kernel: str = "auto", stream=None):
+        import torch
+        self._lib = load_library()
+        sizes = [(int(a), int(b)) for a, b in sizes]
+        self.count = len(sizes)
+        nx = (ctypes.c_int * self.count)(*[a for a, _ in sizes])
+        ny = (ctypes.c_int * self.count)(*[b for _, b in sizes])
+        dxa = None if dx is None else (ctypes.c_double * self.count)(*[float(v) for v in dx])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_batch_create(self.count, nx, ny, dxa, float(E), float(nu),
+                                        KERNELS[kernel], ctypes.c_void_p(stream.cuda_stream),
+                                        ctypes.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, "lbm_batch_create: " + self._lib.lbm_status_string(st).decode())
+        self._h = h
+        self.sizes = sizes
+        self.offsets = [int(self._lib.lbm_batch_offset(h, i)) for i in range(self.count + 1)]
+        self.total = self.offsets[-1]
+
+    def _check(self, st, what):
+        if st != LBM_OK:
+            raise LBMError(st, "%s: %s" % (what, self._lib.lbm_status_string(st).decode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_force(self, F):
+        self._check(self._lib.lbm_batch_set_force(self._h, _dev_ptr(F, 2 * self.total)), "set_force")
+
+    def set_target(self, dstar):
+        self._check(self._lib.lbm_batch_set_target(self._h, _dev_ptr(dstar, 2 * self.total)),
+                    "set_target")
+
+    def primal(self, sweeps: int):
+        self._check(self._lib.lbm_batch_primal(self._h, int(sweeps)), "primal")
+
+    def adjoint(self, sweeps: int):
+        self._check(self._lib.lbm_batch_adjoint(self._h, int(sweeps)), "adjoint")
+
+    def objective(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.count, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lbm_batch_objective(self._h, _dev_ptr(out, self.count)), "objective")
+        return out
+
+    def gradient(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(2 * self.total, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lbm_batch_gradient(self._h, _dev_ptr(out, 2 * self.total)), "gradient")
+        return out
+
+    def get_populations(self, which: int = 0, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(8 * self.total, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lbm_batch_get_populations(self._h, int(which),
+                                                        _dev_ptr(out, 8 * self.total)),
+                    "get_populations")
+        return out
+
+    def tune(self, sweeps: int = 16) -> int:
+        bx = ctypes.c_int()
+        self._check(self._lib.lbm_batch_tune(self._h, int(sweeps), ctypes.byref(bx)), "tune")
+        return bx.value
+
+    # views of one instance inside concatenated arrays
+    def pop_view(self, t, i):
+        o, n = self.offsets[i], self.offsets[i + 1] - self.offsets[i]
+        return t[8 * o: 8 * (o + n)].view(8, n)
+
+    def field_view(self, t, i):
+        o, n = self.offsets[i], self.offsets[i + 1] - self.offsets[i]
+        return t[2 * o: 2 * (o + n)].view(2, n)
+
+
+class UNet:
+    """The warm-start network (include/lbm_solid.h, "Learned warm start"): FP32 CUDA tensors
+    x (B, H, W, 2) and y, t (B, H, W, 8), NHWC."""
+
+    def __init__(self, batch: int, H: int, W: int, base: int = 32, levels: int = 4,
+                 seed: int = 0, stream=None):
+        import torch
+        self._lib = load_library()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.batch, self.H, self.W, self.base, self.levels = batch, H, W, base, levels
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_unet_create(int(base), int(levels), int(batch), int(H), int(W),
+                                       int(seed), ctypes.c_void_p(stream.cuda_stream),
+                                       ctypes.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, "lbm_unet_create: " + self._lib.lbm_status_string(st).decode())
+        self._h = h
+        self.nparams = int(self._lib.lbm_unet_param_count(h))
+        self._loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def _check(self, st, what):
+        if st != LBM_OK:
+            raise LBMError(st, "%s: %s" % (what, self._lib.lbm_status_string(st).decode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f32(self, t, n):
+        import torch
+        return _dev_ptr(t, n, torch.float32)
+
+    def params(self, which: int = 0):
+        """Copy of the FP32 parameter vector (0) or of the last gradient (1)."""
+        import torch
+        out = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        self._check(self._lib.lbm_unet_get_params(self._h, self._f32(out, self.nparams), which),
+                    "get_params")
+        return out
+
+    def set_params(self, p):
+        self._check(self._lib.lbm_unet_set_params(self._h, self._f32(p, self.nparams)),
+                    "set_params")
+
+    def forward(self, x, out=None):
+        import torch
+        P = self.batch * self.H * self.W
+        if out is None:
+            out = torch.empty((self.batch, self.H, self.W, 8), dtype=torch.float32, device="cuda")
+        self._check(self._lib.lbm_unet_forward(self._h, self._f32(x, 2 * P), self._f32(out, 8 * P)),
+                    "forward")
+        return out
+
+    def train_step(self, x, t, lr: float):
+        """One step; returns the loss as a 1-element device tensor (no synchronisation)."""
+        P = self.batch * self.H * self.W
+        self._check(self._lib.lbm_unet_train_step(self._h, self._f32(x, 2 * P), self._f32(t, 8 * P),
+                                                  float(lr), self._f32(self._loss, 1)),
+                    "train_step")
+        return self._loss

@@ -1,0 +1,237 @@
+"""Learned warm start of the primal and adjoint fixed-point iterations.
+
+Not part of the paper's method: a network only proposes the initial populations; the
+solver then iterates (primal collide + stream, Section 3.1; adjoint, Eq.
+adjoint_iteration) to the same residual tolerance as from a cold start, so the fixed
+point, and every objective and gradient computed from it, is the solver's own.  The
+network changes iteration counts only.
+
+Pieces (all arithmetic in the CUDA library, see include/lbm_solid.h "Learned warm
+start"; this module orchestrates):
+
+- ``WarmStartNet``: one U-Net (BF16 storage, FP32 accumulation) for the primal map
+  force F -> steady f_S, or for the adjoint map source r -> steady phi_C, with its
+  training data generated by the solver itself (a batch of periodic lattices driven by
+  random smooth fields, iterated to near steady state) and trained by the library's
+  own forward/backward/Adam kernels.  A network trained on nx^2 lattices is used on
+  (factor * nx)^2 lattices by block-averaging the input and interpolating the predicted
+  moments, which are scaled so that they do not depend on the grid spacing.
+- ``WarmStarter``: supplies initial states to the solves of an optimisation loop.
+  Since the steady states are linear in F (primal) and in r (adjoint), the state of a
+  new control is the previous steady state plus the state of the change; with
+  ``reuse`` the network predicts only the change's state, so its error is relative to
+  the change, not to the whole state.
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional
+
+import numpy as np
+
+from . import inputs as I
+from . import lbm as L
+
+
+def _ptr(t):
+    return L.ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class WarmStartNet:
+    """A U-Net for one of the two fixed-point maps of a periodic nx x nx lattice."""
+
+    def __init__(self, kind: str = "primal", nx: int = 128, E: float = 8.0 / 3.0,
+                 nu: float = 1.0 / 3.0, base: int = 32, levels: int = 4, batch: int = 16,
+                 seed: int = 0, stream=None):
+        import torch
+        if kind not in ("primal", "adjoint"):
+            raise ValueError("kind must be 'primal' or 'adjoint'")
+        self._lib = L.load_library()
+        self.kind, self.nx, self.dx = kind, int(nx), 1.0 / nx
+        self.E, self.nu = float(E), float(nu)
+        self.base, self.levels, self.batch, self.seed = base, levels, batch, seed
+        self.mode = 1 if kind == "primal" else 2  # resolution-free moments, see lbm_warm.cu
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.net = L.UNet(batch, nx, nx, base, levels, seed, stream=self.stream)
+        self._infer: Optional[L.UNet] = None
+        self.chan = None  # per-channel constants c_i (8 floats, device)
+        self._x = torch.empty((1, nx, nx, 2), dtype=torch.float32, device="cuda")
+        self._y = torch.empty((1, nx, nx, 8), dtype=torch.float32, device="cuda")
+        self._s = torch.empty(1, dtype=torch.float32, device="cuda")
+
+    def _st(self):
+        return L.ctypes.c_void_p(self.stream.cuda_stream)
+
+    def _check(self, st, what):
+        if st != L.LBM_OK:
+            raise L.LBMError(st, "%s: %s" % (what, self._lib.lbm_status_string(st).decode()))
+
+    # ---- data -------------------------------------------------------------------
+    def generate(self, count: int, sweeps: int, seed: int = 1, chunk: int = 256,
+                 modes: int = 8, kmax: int = 8):
+        """`count` (input, target) pairs from the solver: random smooth fields (``modes``
+        Fourier modes, |k| up to kmax * 2 pi) drive a batch of lattices for `sweeps`
+        sweeps from rest.  Returns device tensors X (count, nx, nx, 2) and
+        T (count, nx, nx, 8), FP32."""
+        import torch
+        nx, N = self.nx, self.nx * self.nx
+        X = torch.empty((count, nx, nx, 2), dtype=torch.float32, device="cuda")
+        T = torch.empty((count, nx, nx, 8), dtype=torch.float32, device="cuda")
+        sc = torch.empty(chunk, dtype=torch.float32, device="cuda")
+        for start in range(0, count, chunk):
+            m = min(chunk, count - start)
+            fields = I.fourier_fields(m, nx, seed=seed * 1_000_003 + start, modes=modes,
+                                      kmax=kmax, unit_norm=self.kind == "adjoint")
+            b = L.LBMBatch([(nx, nx)] * m, self.E, self.nu, dx=[self.dx] * m, stream=self.stream)
+            if self.kind == "primal":
+                b.set_force(fields.reshape(-1))
+                b.primal(sweeps)
+                pops = b.get_populations(0)
+                src = fields
+            else:
+                # F = 0 keeps d = 0, so r = (dx^2/Cbar)(0 - d*) = -d* for a unit-norm d*
+                b.set_force(torch.zeros(2 * m * N, dtype=torch.float64, device="cuda"))
+                b.set_target(fields.reshape(-1))
+                b.adjoint(sweeps)
+                pops = b.get_populations(2)
+                src = -fields
+            self._check(self._lib.lbm_warm_encode(m, nx, nx, 1, _ptr(src), None, _ptr(X[start:]),
+                                                  _ptr(sc), self._st()), "encode")
+            if self.chan is None:
+                self._check(self._lib.lbm_warm_targets(m, nx, nx, self.dx, self.mode, _ptr(pops),
+                                                       _ptr(sc), None, _ptr(T[start:]),
+                                                       self._st()), "targets")
+                rms = torch.empty(8, dtype=torch.float32, device="cuda")
+                self._check(self._lib.lbm_warm_channel_rms(_ptr(T[start:]), m * N, _ptr(rms),
+                                                           self._st()), "channel_rms")
+                r = rms.cpu().numpy()
+                # channels that vanish identically at the fixed point (the adjoint's
+                # m12 - (1 - theta) m10, m21 - (1 - theta) m01) are not predicted: c_i = 0
+                r = np.where(r > 1e-6 * r.max(), r, 0.0)
+                self.chan = torch.as_tensor(r.astype(np.float32), device="cuda")
+            self._check(self._lib.lbm_warm_targets(m, nx, nx, self.dx, self.mode, _ptr(pops),
+                                                   _ptr(sc), _ptr(self.chan), _ptr(T[start:]),
+                                                   self._st()), "targets")
+            b.close()
+        return X, T
+
+    # ---- training ---------------------------------------------------------------
+    def fit(self, X, T, steps: int, lr: float = 1e-3, lr_min: float = 1e-5,
+            log_every: int = 50, seed: int = 0):
+        """Adam on mini-batches of the data set with a cosine learning-rate schedule.
+        Returns the logged losses [(step, loss)]."""
+        B = self.batch
+        nb = X.shape[0] // B
+        if nb < 1:
+            raise ValueError("need at least one full batch of %d samples" % B)
+        rng = np.random.default_rng(seed)
+        order = rng.permutation(nb)
+        log = []
+        for it in range(steps):
+            if it and it % nb == 0:
+                order = rng.permutation(nb)
+            j = int(order[it % nb])
+            lr_t = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * it / steps))
+            loss = self.net.train_step(X[j * B:(j + 1) * B], T[j * B:(j + 1) * B], lr_t)
+            if it % log_every == 0 or it == steps - 1:
+                log.append((it, float(loss)))
+        self._infer = None
+        return log
+
+    def evaluate(self, X, T):
+        """Relative L2 error of the predictions over a data set (full batches)."""
+        import torch
+        B = self.batch
+        num = den = 0.0
+        out = torch.empty((B,) + tuple(T.shape[1:]), dtype=torch.float32, device="cuda")
+        for j in range(X.shape[0] // B):
+            self.net.forward(X[j * B:(j + 1) * B], out)
+            t = T[j * B:(j + 1) * B]
+            num += float(torch.sum((out.double() - t.double()) ** 2))
+            den += float(torch.sum(t.double() ** 2))
+        return math.sqrt(num / den)
+
+    # ---- inference ---------------------------------------------------------------
+    def _inference_net(self):
+        if self._infer is None:
+            self._infer = L.UNet(1, self.nx, self.nx, self.base, self.levels, self.seed,
+                                 stream=self.stream)
+            self._infer.set_params(self.net.params(0))
+        return self._infer
+
+    def predict(self, field, out, nx_fine: Optional[int] = None, dx_fine: Optional[float] = None,
+                ref=None, accumulate: bool = False):
+        """Initial populations (8 N_fine, FP64 device tensor `out`) for the state driven by
+        `field` (2 N_fine; minus `ref` if given) on an nx_fine^2 periodic lattice with
+        spacing dx_fine (default 1/nx_fine); added to `out` if accumulate."""
+        if self.chan is None:
+            raise RuntimeError("the network has no data normalisation yet: call generate()")
+        nxf = self.nx if nx_fine is None else int(nx_fine)
+        if nxf % self.nx:
+            raise ValueError("lattice size %d is not a multiple of the network's %d" % (nxf, self.nx))
+        factor = nxf // self.nx
+        dxf = 1.0 / nxf if dx_fine is None else float(dx_fine)
+        net = self._inference_net()
+        self._check(self._lib.lbm_warm_encode(1, nxf, nxf, factor, _ptr(field), _ptr(ref),
+                                              _ptr(self._x), _ptr(self._s), self._st()), "encode")
+        net.forward(self._x, self._y)
+        self._check(self._lib.lbm_warm_decode(1, self.nx, self.nx, factor, dxf, self.mode,
+                                              _ptr(self._y), _ptr(self._s), _ptr(self.chan),
+                                              _ptr(out), 1 if accumulate else 0, self._st()),
+                    "decode")
+        return out
+
+
+class WarmStarter:
+    """Initial states for the solves of an optimisation loop over a FORCE_FIELD control.
+
+    primal / adjoint: trained ``WarmStartNet`` or None.  reuse: start from the previous
+    steady state (plus the network's state of the change, when there is a network).
+    With neither a network nor reuse every solve starts from rest, as in the paper."""
+
+    def __init__(self, primal: Optional[WarmStartNet] = None,
+                 adjoint: Optional[WarmStartNet] = None, reuse: bool = True):
+        self.primal, self.adjoint, self.reuse = primal, adjoint, reuse
+        self.F_prev = self.f_prev = self.r_prev = self.p_prev = None
+
+    def before_primal(self, solver, F):
+        if self.primal is None and not (self.reuse and self.f_prev is not None):
+            return
+        if self.reuse and self.f_prev is not None:
+            f0 = self.f_prev.clone()
+            if self.primal is not None:
+                self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx, ref=self.F_prev,
+                                    accumulate=True)
+        else:
+            import torch
+            f0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
+            self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx)
+        solver.set_populations(0, f0)
+
+    def after_primal(self, solver, F):
+        if self.reuse:
+            self.F_prev = F.detach().clone()
+            self.f_prev = solver.get_populations(0).clone()
+
+    def before_adjoint(self, solver):
+        if self.adjoint is None and not (self.reuse and self.p_prev is not None):
+            return
+        r = solver.adjoint_source()
+        if self.reuse and self.p_prev is not None:
+            p0 = self.p_prev.clone()
+            if self.adjoint is not None:
+                self.adjoint.predict(r, p0, ref=self.r_prev, accumulate=True)
+        else:
+            import torch
+            p0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
+            self.adjoint.predict(r, p0)
+        solver.set_populations(2, p0)
+        self._r = r
+
+    def after_adjoint(self, solver):
+        if self.reuse:
+            self.r_prev = getattr(self, "_r", None)
+            if self.r_prev is None:
+                self.r_prev = solver.adjoint_source()
+            self.p_prev = solver.get_populations(2).clone()
+            self._r = None

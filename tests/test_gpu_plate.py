@@ -42,7 +42,7 @@ def lbm_mod():
 def paper_plate(Nx, E=I.PLATE_E, nu=I.PLATE_NU):
     geo = I.plate_geometry(Nx)
     dstar, sigma, F = I.plate_manufactured(geo.X, geo.Y, E=E, nu=nu)
-    wd, wT = I.plate_wall_data(geo, dstar, sigma)
+    wd, wT = I.plate_wall_data(geo, E=E, nu=nu)
     return geo, dstar, F * geo.active, wd, wT
 
 

@@ -67,7 +67,7 @@ def test_plate_field_gradient_matches_fad(lbm_mod):
     geo = I.plate_geometry(Nx)
     dstar, sigma, F = I.plate_manufactured(geo.X, geo.Y)
     F = F * geo.active
-    wd, wT = I.plate_wall_data(geo, dstar, sigma)
+    wd, wT = I.plate_wall_data(geo)
     N = geo.nx * geo.nx
     E = I.lognormal_E(N, E_ref=0.08, sigma=0.2, seed=0)  # tau_s stays below 1/2
     alpha = np.sqrt(E)

@@ -22,7 +22,7 @@ from paper_2609_31347_b300 import inputs as I
 def plate_grid(Nx, E=I.PLATE_E, nu=I.PLATE_NU):
     geo = I.plate_geometry(Nx)
     dstar, sigma, F = I.plate_manufactured(geo.X, geo.Y, E=E, nu=nu)
-    wd, wT = I.plate_wall_data(geo, dstar, sigma)
+    wd, wT = I.plate_wall_data(geo, E=E, nu=nu)
     g = oracle.Grid(geo.nx, geo.nx, geo.dx, nu, periodic=False, node_type=geo.node_type,
                     link=geo.link, wall_d=wd, wall_T=wT, wall_n=geo.normal)
     return g, geo, dstar, F * geo.active

@@ -87,6 +87,32 @@ def test_single_wavenumber_is_preserved():
     assert 3.5 < amp_err[0] / amp_err[1] < 4.5 and 3.5 < amp_err[1] / amp_err[2] < 4.5
 
 
+@pytest.mark.parametrize("axis", [0, 1])
+def test_half_nyquist_force_is_never_damped(axis):
+    # Degenerate case of the periodic scheme (Section 3.1 collision with omega_12 =
+    # omega_21 = omega_f = 1, no rest population): at the wavevectors (N/2, 0) and
+    # (0, N/2) one step multiplies a collision invariant by -1 under streaming, so the
+    # iteration has the eigenvalue -1 there.  A force with that content is never
+    # converged by iterating: the iterates alternate about the fixed point, which is
+    # still well defined (I - P A has the eigenvalue 2 there) and is their average.
+    nx, E, nu = 8, 8.0 / 3.0, 1.0 / 3.0
+    g = oracle.Grid(nx, nx, 1.0 / nx, nu)
+    i = np.arange(nx)
+    X, Y = np.meshgrid(i, i, indexing="xy")
+    F = np.zeros((2, nx * nx))
+    F[axis] = ((-1.0) ** (X if axis == 0 else Y)).ravel()  # zero mean
+    f = [oracle.primal(g, E, F, T) for T in (300, 301, 302)]
+    scale = np.abs(f[1]).max()
+    assert np.abs(f[2] - f[0]).max() <= 1e-12 * scale       # period two ...
+    assert np.abs(f[1] - f[0]).max() >= 0.5 * scale          # ... and no decay
+    fp = fourier.periodic_fixed_point(nx, E, nu, F)
+    assert np.abs(0.5 * (f[0] + f[1]) - fp).max() <= 1e-12 * scale
+    # any smooth force on the same grid converges
+    Fs = I.fourier_force(nx, seed=3, kmax=2)
+    a, b = oracle.primal(g, E, Fs, 400), oracle.primal(g, E, Fs, 401)
+    assert np.abs(b - a).max() <= 1e-13 * np.abs(b).max()
+
+
 def test_monitor_is_mean_squared_displacement():
     nx = 6
     rng = np.random.default_rng(0)
