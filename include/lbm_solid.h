@@ -234,7 +234,8 @@ lbm_status lbm_batch_tune(lbm_batch *b, int sweeps, int *best_bx);
  * residual tolerance as from a cold start, so it changes iteration counts, never the
  * fixed point.  A linear U-Net: `levels` levels of C_l = base * 2^l channels; per level
  * two 3x3 convolutions with circular padding and bias, 2x2 average pooling between
- * levels; decoder: nearest 2x upsampling, concatenation [upsampled, skip], two 3x3
+ * levels; decoder: bilinear 2x upsampling (periodic, coarse values at the centres of
+ * their 2x2 blocks), concatenation [upsampled, skip], two 3x3
  * convolutions; a 1x1 head to 8 channels.  Input 2 channels, output 8.  BF16 weights
  * and activations, FP32 accumulation on the tensor cores, FP32 master weights and Adam.
  *
@@ -257,8 +258,14 @@ long lbm_unet_param_count(const lbm_unet *u); /* -1 for NULL */
 lbm_status lbm_unet_get_params(lbm_unet *u, float *dst_dev, int which);
 /* Replaces the parameter vector (Adam moments are kept). */
 lbm_status lbm_unet_set_params(lbm_unet *u, const float *src_dev);
-/* y = net(x); y_dev may be NULL (the output then stays internal). */
-lbm_status lbm_unet_forward(lbm_unet *u, const float *x_dev, float *y_dev);
+/* y = net(x); y_dev may be NULL (the output then stays internal).  exact_acts = 0:
+   BF16 activations, as in training.  exact_acts = 1: FP32 activations, each product
+   taken as two BF16 products (high and low part of the activation), so that apart from
+   the FP32 sums the network is the exact linear map of its BF16 weights; BF16 rounding
+   of activations adds broadband noise (about 1e-3 relative, at every wavevector), which
+   a warm start must not carry into the slowly decaying modes.  The FP32 activation
+   buffers are allocated on the first such call (LBM_ERR_OOM if that fails). */
+lbm_status lbm_unet_forward(lbm_unet *u, const float *x_dev, float *y_dev, int exact_acts);
 /* Forward, loss L = (1/2) mean (y - t)^2 into loss_dev (may be NULL), gradient of L
    w.r.t. every parameter (readable with get_params(which = 1)), then one Adam step
    (beta 0.9 / 0.999, eps 1e-8) with learning rate lr if lr > 0. */
@@ -295,7 +302,14 @@ lbm_status lbm_warm_targets(int count, int nx, int ny, double dx, int mode,
 /* Populations (count, 8, hc*factor, wc*factor) from network output y (count, hc, wc, 8):
    periodic bilinear interpolation to the fine nodes (coarse node j = centre of its
    block), times s_b c_i, moments rescaled with the fine spacing dx_fine, inverted;
-   written to pop_dev, or added to it if accumulate is nonzero. */
+   written to pop_dev, or added to it if accumulate is nonzero.  For modes 1 and 2 the
+   result's Fourier components at the wavevectors (nx/2, 0) and (0, ny/2) are then removed
+   from every population plane (even sizes): the primal and adjoint steps have the
+   eigenvalue -1 there, so an initial error in them would never decay, and the steady
+   state of a smooth field has none.  Last, the conserved k = 0 components (the mean
+   displacement: mean m10, m01 of f_S for mode 1, the matching adjoint invariants for
+   mode 2) are set to zero, their value when iterating from rest with a zero-mean force
+   or source; otherwise the iteration would settle on a rigidly shifted state. */
 lbm_status lbm_warm_decode(int count, int wc, int hc, int factor, double dx_fine, int mode,
                            const float *y_dev, const float *scale_dev, const float *chan_dev,
                            double *pop_dev, int accumulate, void *stream);

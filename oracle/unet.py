@@ -6,7 +6,10 @@ requested residual.  The network is a 4-level U-Net:
 
   level l (l = 0..3) has C_l = base * 2^l channels and two 3x3 convolutions;
   encoder: conv(2 or C_{l-1} -> C_l), conv(C_l -> C_l), then 2x2 average pooling;
-  decoder: nearest 2x upsampling, concatenation [up, skip_l], conv(C_{l+1} + C_l -> C_l),
+  decoder: bilinear 2x upsampling (periodic; each coarse value sits at the centre of its
+           2x2 fine block, so fine cells take 3/4 of their own coarse cell and 1/4 of
+           the neighbour on their side, per axis), concatenation [up, skip_l],
+           conv(C_{l+1} + C_l -> C_l),
            conv(C_l -> C_l);
   head: 1x1 convolution C_0 -> 8.
 
@@ -85,13 +88,35 @@ def pool_backward(g):
     return np.repeat(np.repeat(g, 2, axis=1), 2, axis=2) * 0.25
 
 
+def _up_axis(x, axis):
+    # linear 2x interpolation with the coarse value at the centre of its two fine cells
+    # (fine 2j at -1/4, fine 2j+1 at +1/4 coarse cells from coarse j), periodic
+    even = 0.75 * x + 0.25 * np.roll(x, 1, axis=axis)   # 3/4 x[j] + 1/4 x[j-1]
+    odd = 0.75 * x + 0.25 * np.roll(x, -1, axis=axis)   # 3/4 x[j] + 1/4 x[j+1]
+    out = np.stack([even, odd], axis=axis + 1)
+    shape = list(x.shape)
+    shape[axis] *= 2
+    return out.reshape(shape)
+
+
+def _up_axis_backward(g, axis):
+    shape = list(g.shape)
+    shape[axis] //= 2
+    shape.insert(axis + 1, 2)
+    gr = g.reshape(shape)
+    ge = np.take(gr, 0, axis=axis + 1)
+    go = np.take(gr, 1, axis=axis + 1)
+    # transpose of _up_axis: x[j] feeds even[j], odd[j] (3/4), even[j+1], odd[j-1] (1/4)
+    return 0.75 * (ge + go) + 0.25 * (np.roll(ge, -1, axis=axis) + np.roll(go, 1, axis=axis))
+
+
 def up(x):
-    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+    """Bilinear 2x upsampling of (B, H, W, C), periodic."""
+    return _up_axis(_up_axis(x, 1), 2)
 
 
 def up_backward(g):
-    B, H, W, C = g.shape
-    return g.reshape(B, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
+    return _up_axis_backward(_up_axis_backward(g, 2), 1)
 
 
 def forward(params, x, levels: int = 4, keep: bool = False):

@@ -191,6 +191,11 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *smem /* >= 32
   }
 }
 
+// max that propagates NaN (fmax drops it), so that a blown-up state reaches the monitor
+__device__ __forceinline__ double nan_max(double a, double b) {
+  return (a != a || b != b) ? a + b : fmax(a, b);
+}
+
 template <int NV>
 __device__ __forceinline__ void block_max(double (&v)[NV], double *smem) {
   const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
@@ -198,7 +203,7 @@ __device__ __forceinline__ void block_max(double (&v)[NV], double *smem) {
   const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i)
-    for (int o = 16; o > 0; o >>= 1) v[i] = fmax(v[i], __shfl_down_sync(0xffffffffu, v[i], o));
+    for (int o = 16; o > 0; o >>= 1) v[i] = nan_max(v[i], __shfl_down_sync(0xffffffffu, v[i], o));
   if (lane == 0)
     for (int i = 0; i < NV; ++i) smem[warp * NV + i] = v[i];
   __syncthreads();
@@ -206,7 +211,7 @@ __device__ __forceinline__ void block_max(double (&v)[NV], double *smem) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       v[i] = lane < nwarps ? smem[lane * NV + i] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) v[i] = fmax(v[i], __shfl_down_sync(0xffffffffu, v[i], o));
+      for (int o = 16; o > 0; o >>= 1) v[i] = nan_max(v[i], __shfl_down_sync(0xffffffffu, v[i], o));
     }
   }
 }

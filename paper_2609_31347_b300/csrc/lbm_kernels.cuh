@@ -631,8 +631,8 @@ static __global__ void __launch_bounds__(256) k_residual(const double *__restric
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
        i += (long)gridDim.x * blockDim.x) {
     const double ai = a[i];
-    v[0] = fmax(v[0], fabs(ai - bb[i]));
-    v[1] = fmax(v[1], fabs(ai));
+    v[0] = nan_max(v[0], fabs(ai - bb[i]));
+    v[1] = nan_max(v[1], fabs(ai));
   }
   __shared__ double sm[64];
   block_max<2>(v, sm);
@@ -651,7 +651,7 @@ static __global__ void __launch_bounds__(256) k_finish(const double *__restrict_
     double acc[1] = {0.0};
     for (long i = threadIdx.x; i < nb; i += blockDim.x) {
       const double t = partial[i * nv + v];
-      acc[0] = op == 0 ? acc[0] + t : fmax(acc[0], t);
+      acc[0] = op == 0 ? acc[0] + t : nan_max(acc[0], t);
     }
     if (op == 0)
       block_sum<1>(acc, sm);

@@ -1,5 +1,5 @@
 // Warm-start network on the GPU: a linear 4-level U-Net (3x3 circular convolutions,
-// 2x2 average pooling, nearest upsampling with skip concatenation, 1x1 head) mapping a
+// 2x2 average pooling, bilinear upsampling with skip concatenation, 1x1 head) mapping a
 // 2-channel control field to the 8 steady populations.  BF16 activations and weights,
 // FP32 accumulation with mma.sync.m16n8k16 (implicit GEMM, no im2col buffer), FP32
 // master weights with Adam.  Training and inference kernels are all in this file.
@@ -29,6 +29,25 @@ __device__ __forceinline__ uint32_t pack2(bf16 a, bf16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+__device__ __forceinline__ float ldf(const bf16 &v) { return __bfloat162float(v); }
+__device__ __forceinline__ float ldf(const float &v) { return v; }
+__device__ __forceinline__ void stf(bf16 &d, float v) { d = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void stf(float &d, float v) { d = v; }
+
+// A-operand word (two consecutive k) from BF16 activations, or the high and low BF16
+// parts of two FP32 activations (x = hi + lo to 16 significant bits).
+__device__ __forceinline__ void a_word(const bf16 *p, uint32_t &hi, uint32_t &lo) {
+  hi = *reinterpret_cast<const uint32_t *>(p);
+  lo = 0u;
+}
+__device__ __forceinline__ void a_word(const float *p, uint32_t &hi, uint32_t &lo) {
+  const float2 v = *reinterpret_cast<const float2 *>(p);
+  const bf16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+  hi = pack2(h0, h1);
+  lo = pack2(__float2bfloat16_rn(v.x - __bfloat162float(h0)),
+             __float2bfloat16_rn(v.y - __bfloat162float(h1)));
+}
+
 __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4],
                                          const uint32_t (&b)[2]) {
   asm volatile(
@@ -42,13 +61,17 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4],
 // W[tap][n][k] with p = (b, y, x) and circular wrap in y, x; s = +1 (forward) or -1
 // (gradient w.r.t. the input, with the transposed weight copy).  One warp: 16 pixels
 // along x times 32 output channels (4 n-tiles of 8); grid.y over output-channel tiles.
+// TIN = bf16: BF16 activations, one mma per fragment.  TIN = float: FP32 activations,
+// each A fragment split into high and low BF16 parts and multiplied twice, so that the
+// only rounding left is that of the BF16 weights themselves and the FP32 sums.
 // Requires W % 16 == 0, Cin % 16 == 0, Cout % 8 == 0.
-template <int KS>
-__global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int Cin,
+template <int KS, typename TIN>
+__global__ void __launch_bounds__(128) k_conv(const TIN *__restrict__ in, int Cin,
                                               const bf16 *__restrict__ w, int Cout,
                                               const float *__restrict__ bias,
                                               bf16 *__restrict__ out_bf, float *__restrict__ out_f,
                                               int B, int H, int W, int sgn) {
+  constexpr bool kSplit = sizeof(TIN) == 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const long tile = (long)blockIdx.x * 4 + warp;  // 16-pixel tile
@@ -72,15 +95,15 @@ __global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int C
       const int tap = (dy + R) * KS + (dx + R);
       const int xa = ((x0 + g + sgn * dx) % W + W) % W;
       const int xb = ((x0 + g + 8 + sgn * dx) % W + W) % W;
-      const bf16 *ra = in + (((long)b * H + ys) * W + xa) * Cin;
-      const bf16 *rb = in + (((long)b * H + ys) * W + xb) * Cin;
+      const TIN *ra = in + (((long)b * H + ys) * W + xa) * Cin;
+      const TIN *rb = in + (((long)b * H + ys) * W + xb) * Cin;
       const bf16 *wt = w + (long)tap * Cout * Cin;
       for (int k0 = 0; k0 < Cin; k0 += 16) {
-        uint32_t a[4];
-        a[0] = *reinterpret_cast<const uint32_t *>(ra + k0 + 2 * t);
-        a[1] = *reinterpret_cast<const uint32_t *>(rb + k0 + 2 * t);
-        a[2] = *reinterpret_cast<const uint32_t *>(ra + k0 + 2 * t + 8);
-        a[3] = *reinterpret_cast<const uint32_t *>(rb + k0 + 2 * t + 8);
+        uint32_t a[4], al[4];
+        a_word(ra + k0 + 2 * t, a[0], al[0]);
+        a_word(rb + k0 + 2 * t, a[1], al[1]);
+        a_word(ra + k0 + 2 * t + 8, a[2], al[2]);
+        a_word(rb + k0 + 2 * t + 8, a[3], al[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int n = n0 + 8 * j + g;
@@ -90,6 +113,7 @@ __global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int C
           bb[0] = *reinterpret_cast<const uint32_t *>(wr);
           bb[1] = *reinterpret_cast<const uint32_t *>(wr + 8);
           mma16816(acc[j], a, bb);
+          if (kSplit) mma16816(acc[j], al, bb);
         }
       }
     }
@@ -104,10 +128,8 @@ __global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int C
     const long pa = (((long)b * H + y) * W + x0 + g) * Cout + n;
     const long pb = (((long)b * H + y) * W + x0 + g + 8) * Cout + n;
     if (out_f) {
-      out_f[pa] = acc[j][0] + b0;
-      out_f[pa + 1] = acc[j][1] + b1;
-      out_f[pb] = acc[j][2] + b0;
-      out_f[pb + 1] = acc[j][3] + b1;
+      *reinterpret_cast<float2 *>(out_f + pa) = make_float2(acc[j][0] + b0, acc[j][1] + b1);
+      *reinterpret_cast<float2 *>(out_f + pb) = make_float2(acc[j][2] + b0, acc[j][3] + b1);
     } else {
       *reinterpret_cast<uint32_t *>(out_bf + pa) =
           pack2(__float2bfloat16_rn(acc[j][0] + b0), __float2bfloat16_rn(acc[j][1] + b1));
@@ -192,8 +214,8 @@ __global__ void k_bias_grad(const bf16 *__restrict__ gout, int C, int stride, lo
   atomicAdd(gb + c, s);
 }
 
-__global__ void k_pool(const bf16 *__restrict__ in, bf16 *__restrict__ out, int C, int B, int H,
-                       int W) {
+template <typename T>
+__global__ void k_pool(const T *__restrict__ in, T *__restrict__ out, int C, int B, int H, int W) {
   const int Ho = H / 2, Wo = W / 2;
   const long total = (long)B * Ho * Wo * C;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
@@ -203,17 +225,25 @@ __global__ void k_pool(const bf16 *__restrict__ in, bf16 *__restrict__ out, int 
     const int x = (int)(r % Wo);
     r /= Wo;
     const int y = (int)(r % Ho), b = (int)(r / Ho);
-    const bf16 *s = in + (((long)b * H + 2 * y) * W + 2 * x) * C + c;
-    const float v = __bfloat162float(s[0]) + __bfloat162float(s[C]) +
-                    __bfloat162float(s[(long)W * C]) + __bfloat162float(s[(long)W * C + C]);
-    out[i] = __float2bfloat16_rn(0.25f * v);
+    const T *s = in + (((long)b * H + 2 * y) * W + 2 * x) * C + c;
+    const float v = ldf(s[0]) + ldf(s[C]) + ldf(s[(long)W * C]) + ldf(s[(long)W * C + C]);
+    stf(out[i], 0.25f * v);
   }
 }
 
-// out (B,H,W,Ca+Cb) = [nearest-upsampled a (B,H/2,W/2,Ca), skip (B,H,W,Cb)].
-__global__ void k_up_concat(const bf16 *__restrict__ a, int Ca, const bf16 *__restrict__ s,
-                            int Cb, bf16 *__restrict__ out, int B, int H, int W) {
-  const int C = Ca + Cb;
+// Bilinear 2x upsampling, periodic: each coarse value sits at the centre of its 2x2 fine
+// block, so along each axis fine cell i takes 3/4 of coarse cell i/2 and 1/4 of the
+// coarse neighbour on its side (i even: i/2 - 1, i odd: i/2 + 1).
+__device__ __forceinline__ int up_nbr(int i, int n) {
+  const int j = i >> 1;
+  return (i & 1) ? (j + 1 == n ? 0 : j + 1) : (j == 0 ? n - 1 : j - 1);
+}
+
+// out (B,H,W,Ca+Cb) = [bilinear-upsampled a (B,H/2,W/2,Ca), skip (B,H,W,Cb)].
+template <typename T>
+__global__ void k_up_concat(const T *__restrict__ a, int Ca, const T *__restrict__ s, int Cb,
+                            T *__restrict__ out, int B, int H, int W) {
+  const int C = Ca + Cb, Hc = H / 2, Wc = W / 2;
   const long total = (long)B * H * W * C;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
        i += (long)gridDim.x * blockDim.x) {
@@ -222,17 +252,28 @@ __global__ void k_up_concat(const bf16 *__restrict__ a, int Ca, const bf16 *__re
     const int x = (int)(p % W);
     const long r = p / W;
     const int y = (int)(r % H), b = (int)(r / H);
-    out[i] = c < Ca ? a[(((long)b * (H / 2) + y / 2) * (W / 2) + x / 2) * Ca + c]
-                    : s[p * Cb + (c - Ca)];
+    if (c < Ca) {
+      const int x0 = x >> 1, x1 = up_nbr(x, Wc), y0 = y >> 1, y1 = up_nbr(y, Hc);
+      const T *ab = a + (long)b * Hc * Wc * Ca + c;
+      const float v = 0.5625f * ldf(ab[((long)y0 * Wc + x0) * Ca]) +
+                      0.1875f * (ldf(ab[((long)y0 * Wc + x1) * Ca]) +
+                                 ldf(ab[((long)y1 * Wc + x0) * Ca])) +
+                      0.0625f * ldf(ab[((long)y1 * Wc + x1) * Ca]);
+      stf(out[i], v);
+    } else {
+      out[i] = s[p * Cb + (c - Ca)];
+    }
   }
 }
 
-// Backward of k_up_concat: ga = sum of the 4 fine gradients, gs = its slice (added to the
-// pooled-path gradient by k_pool_back_add).
+// Backward of k_up_concat's upsampled part: coarse cell j gathers fine cells 2j and
+// 2j+1 with weight 3/4 and 2j-1, 2j+2 with 1/4 along each axis (the skip slice of the
+// gradient is read by k_pool_back_add).
 __global__ void k_up_concat_back(const bf16 *__restrict__ g, int Ca, int Cb, bf16 *__restrict__ ga,
                                  int B, int H, int W) {
   const int C = Ca + Cb, Hc = H / 2, Wc = W / 2;
   const long total = (long)B * Hc * Wc * Ca;
+  const float wt[4] = {0.25f, 0.75f, 0.75f, 0.25f};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
        i += (long)gridDim.x * blockDim.x) {
     const int c = (int)(i % Ca);
@@ -240,9 +281,21 @@ __global__ void k_up_concat_back(const bf16 *__restrict__ g, int Ca, int Cb, bf1
     const int x = (int)(r % Wc);
     r /= Wc;
     const int y = (int)(r % Hc), b = (int)(r / Hc);
-    const bf16 *s = g + (((long)b * H + 2 * y) * W + 2 * x) * C + c;
-    const float v = __bfloat162float(s[0]) + __bfloat162float(s[C]) +
-                    __bfloat162float(s[(long)W * C]) + __bfloat162float(s[(long)W * C + C]);
+    const bf16 *gb = g + (long)b * H * W * C + c;
+    float v = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int fy = 2 * y - 1 + u;
+      fy = fy < 0 ? fy + H : (fy >= H ? fy - H : fy);
+      float row = 0.f;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        int fx = 2 * x - 1 + t;
+        fx = fx < 0 ? fx + W : (fx >= W ? fx - W : fx);
+        row += wt[t] * __bfloat162float(gb[((long)fy * W + fx) * C]);
+      }
+      v += wt[u] * row;
+    }
     ga[i] = __float2bfloat16_rn(v);
   }
 }
@@ -264,12 +317,13 @@ __global__ void k_pool_back_add(const bf16 *__restrict__ gcoarse, const bf16 *__
   }
 }
 
-// Input (B,H,W,2) FP32 -> 16-channel BF16 (channels 2..15 zero).
-__global__ void k_pack_input(const float *__restrict__ x, bf16 *__restrict__ out, long P) {
+// Input (B,H,W,2) FP32 -> 16 channels (2..15 zero), BF16 or FP32.
+template <typename T>
+__global__ void k_pack_input(const float *__restrict__ x, T *__restrict__ out, long P) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < P * 16;
        i += (long)gridDim.x * blockDim.x) {
     const int c = (int)(i % 16);
-    out[i] = __float2bfloat16_rn(c < 2 ? x[(i / 16) * 2 + c] : 0.f);
+    stf(out[i], c < 2 ? x[(i / 16) * 2 + c] : 0.f);
   }
 }
 
@@ -360,6 +414,9 @@ struct lbm_unet {
   float *y = nullptr, *partial = nullptr;
   bf16 *x16 = nullptr, *gy = nullptr;
   std::vector<bf16 *> pooled, upcat, gcoarse;  // per level
+  // FP32 activations of the exact-activation forward (allocated on first use)
+  float *x32 = nullptr;
+  std::vector<float *> out32, pooled32, upcat32;
   long step = 0;
   std::vector<void *> allocs;
 };
@@ -379,14 +436,67 @@ T *dalloc(lbm_unet *u, size_t n, cudaError_t &e) {
 
 unsigned gs(long n) { long b = (n + 255) / 256; return (unsigned)(b < 148 * 16 ? (b < 1 ? 1 : b) : 148 * 16); }
 
-void conv_fwd(lbm_unet *u, const Layer &l, const bf16 *in, bf16 *out_bf, float *out_f, int Hh, int Ww) {
+template <typename TIN>
+void conv_fwd(lbm_unet *u, const Layer &l, const TIN *in, bf16 *out_bf, float *out_f, int Hh, int Ww) {
   const long tiles = (long)u->B * Hh * (Ww / 16);
   dim3 grid((unsigned)((tiles + 3) / 4), (unsigned)((l.co + 31) / 32));
   const float *bias = u->p + l.boff;
   if (l.ks == 3)
-    k_conv<3><<<grid, 128, 0, u->stream>>>(in, l.cipad, l.wf, l.co, bias, out_bf, out_f, u->B, Hh, Ww, 1);
+    k_conv<3, TIN><<<grid, 128, 0, u->stream>>>(in, l.cipad, l.wf, l.co, bias, out_bf, out_f, u->B, Hh, Ww, 1);
   else
-    k_conv<1><<<grid, 128, 0, u->stream>>>(in, l.cipad, l.wf, l.co, bias, out_bf, out_f, u->B, Hh, Ww, 1);
+    k_conv<1, TIN><<<grid, 128, 0, u->stream>>>(in, l.cipad, l.wf, l.co, bias, out_bf, out_f, u->B, Hh, Ww, 1);
+}
+
+// a layer's output in the activation type of the pass
+void conv_out(lbm_unet *u, const Layer &l, const bf16 *in, bf16 *out, int Hh, int Ww) {
+  conv_fwd<bf16>(u, l, in, out, nullptr, Hh, Ww);
+}
+void conv_out(lbm_unet *u, const Layer &l, const float *in, float *out, int Hh, int Ww) {
+  conv_fwd<float>(u, l, in, nullptr, out, Hh, Ww);
+}
+
+// Forward pass with activations of type T: BF16 (training; the layer inputs are kept
+// for the backward pass) or FP32 (exact activations).  outs[i]: output of layer i.
+template <typename T>
+void forward_t(lbm_unet *u, const float *x, T *xin, const std::vector<T *> &outs,
+               const std::vector<T *> &pooled, const std::vector<T *> &upcat, bool save) {
+  const int lv = u->levels;
+  const long P = (long)u->B * u->H * u->W;
+  k_pack_input<T><<<gs(P * 16), 256, 0, u->stream>>>(x, xin, P);
+  const T *h = xin;
+  int li = 0;
+  auto keep = [&](Layer &ly, const T *in) {
+    if (save) ly.in = reinterpret_cast<bf16 *>(const_cast<T *>(in));
+  };
+  for (int l = 0; l < lv; ++l) {
+    const int ia = li++, ib = li++;
+    Layer &a = u->L[ia], &b = u->L[ib];
+    keep(a, h);
+    conv_out(u, a, h, outs[ia], a.H, a.W);
+    keep(b, outs[ia]);
+    conv_out(u, b, outs[ia], outs[ib], b.H, b.W);
+    h = outs[ib];
+    if (l + 1 < lv) {
+      k_pool<T><<<gs((long)u->B * b.H * b.W * b.co / 4), 256, 0, u->stream>>>(h, pooled[l], b.co,
+                                                                              u->B, b.H, b.W);
+      h = pooled[l];
+    }
+  }
+  for (int l = lv - 2; l >= 0; --l) {
+    const int ia = li++, ib = li++;
+    Layer &a = u->L[ia], &b = u->L[ib];
+    const int cu = a.ci - u->L[2 * l + 1].co;  // channels of the upsampled path
+    k_up_concat<T><<<gs((long)u->B * a.H * a.W * a.ci), 256, 0, u->stream>>>(
+        h, cu, outs[2 * l + 1], a.ci - cu, upcat[l], u->B, a.H, a.W);
+    keep(a, upcat[l]);
+    conv_out(u, a, upcat[l], outs[ia], a.H, a.W);
+    keep(b, outs[ia]);
+    conv_out(u, b, outs[ia], outs[ib], b.H, b.W);
+    h = outs[ib];
+  }
+  Layer &hd = u->L[li];
+  keep(hd, h);
+  conv_fwd<T>(u, hd, h, nullptr, u->y, hd.H, hd.W);
 }
 
 // gradient w.r.t. the input of layer l (output in gin, cipad channels), and weight/bias
@@ -397,9 +507,9 @@ void conv_bwd(lbm_unet *u, Layer &l, const bf16 *gout, int Hh, int Ww, bool need
     const long tiles = P / 16;
     dim3 grid((unsigned)((tiles + 3) / 4), (unsigned)((l.cipad + 31) / 32));
     if (l.ks == 3)
-      k_conv<3><<<grid, 128, 0, u->stream>>>(gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, u->B, Hh, Ww, -1);
+      k_conv<3, bf16><<<grid, 128, 0, u->stream>>>(gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, u->B, Hh, Ww, -1);
     else
-      k_conv<1><<<grid, 128, 0, u->stream>>>(gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, u->B, Hh, Ww, -1);
+      k_conv<1, bf16><<<grid, 128, 0, u->stream>>>(gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, u->B, Hh, Ww, -1);
   }
   const long chunks = (P + 255) / 256;
   const unsigned nci = (unsigned)((l.cipad + 63) / 64);
@@ -531,39 +641,33 @@ lbm_status lbm_unet_set_params(lbm_unet *u, const float *src) {
 }
 
 // Forward pass: x (B,H,W,2) FP32 -> y (B,H,W,8) FP32 (y_dev may be NULL: kept inside).
-lbm_status lbm_unet_forward(lbm_unet *u, const float *x, float *y_out) {
+// exact_acts = 0: BF16 activations (the training pass); 1: FP32 activations.
+lbm_status lbm_unet_forward(lbm_unet *u, const float *x, float *y_out, int exact_acts) {
   if (!u || !x) return LBM_ERR_ARG;
-  const int lv = u->levels;
   const long P = (long)u->B * u->H * u->W;
-  k_pack_input<<<gs(P * 16), 256, 0, u->stream>>>(x, u->x16, P);
-  const bf16 *h = u->x16;
-  int li = 0;
-  for (int l = 0; l < lv; ++l) {
-    Layer &a = u->L[li++], &b = u->L[li++];
-    a.in = const_cast<bf16 *>(h);
-    conv_fwd(u, a, h, a.out, nullptr, a.H, a.W);
-    b.in = a.out;
-    conv_fwd(u, b, a.out, b.out, nullptr, b.H, b.W);
-    h = b.out;
-    if (l + 1 < lv) {
-      k_pool<<<gs((long)u->B * b.H * b.W * b.co / 4), 256, 0, u->stream>>>(h, u->pooled[l], b.co, u->B, b.H, b.W);
-      h = u->pooled[l];
+  if (exact_acts) {
+    if (!u->x32) {
+      cudaError_t e = cudaSuccess;
+      u->x32 = dalloc<float>(u, P * 16, e);
+      for (auto &ly : u->L) u->out32.push_back(dalloc<float>(u, (long)u->B * ly.H * ly.W * ly.co, e));
+      for (int l = 0; l < u->levels; ++l) {
+        const long Pl = (long)u->B * (u->H >> l) * (u->W >> l);
+        const int c = u->base << l;
+        u->pooled32.push_back(l + 1 < u->levels ? dalloc<float>(u, Pl / 4 * c, e) : nullptr);
+        u->upcat32.push_back(l + 1 < u->levels ? dalloc<float>(u, Pl * (c + 2 * c), e) : nullptr);
+      }
+      if (e != cudaSuccess) {
+        u->x32 = nullptr;  // buffers stay in allocs and are freed by destroy
+        u->out32.clear(); u->pooled32.clear(); u->upcat32.clear();
+        return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+      }
     }
+    forward_t<float>(u, x, u->x32, u->out32, u->pooled32, u->upcat32, false);
+  } else {
+    std::vector<bf16 *> outs;
+    for (auto &ly : u->L) outs.push_back(ly.out);
+    forward_t<bf16>(u, x, u->x16, outs, u->pooled, u->upcat, true);
   }
-  for (int l = lv - 2; l >= 0; --l) {
-    Layer &a = u->L[li++], &b = u->L[li++];
-    const int cu = a.ci - u->L[2 * l + 1].co;  // channels of the upsampled path
-    k_up_concat<<<gs((long)u->B * a.H * a.W * a.ci), 256, 0, u->stream>>>(
-        h, cu, u->L[2 * l + 1].out, a.ci - cu, u->upcat[l], u->B, a.H, a.W);
-    a.in = u->upcat[l];
-    conv_fwd(u, a, a.in, a.out, nullptr, a.H, a.W);
-    b.in = a.out;
-    conv_fwd(u, b, a.out, b.out, nullptr, b.H, b.W);
-    h = b.out;
-  }
-  Layer &hd = u->L[li];
-  hd.in = const_cast<bf16 *>(h);
-  conv_fwd(u, hd, h, nullptr, u->y, hd.H, hd.W);
   if (y_out &&
       cudaMemcpyAsync(y_out, u->y, sizeof(float) * P * 8, cudaMemcpyDeviceToDevice, u->stream) !=
           cudaSuccess)
@@ -576,7 +680,7 @@ lbm_status lbm_unet_forward(lbm_unet *u, const float *x, float *y_out) {
 lbm_status lbm_unet_train_step(lbm_unet *u, const float *x, const float *t, float lr,
                                float *loss_dev) {
   if (!u || !x || !t) return LBM_ERR_ARG;
-  lbm_status st = lbm_unet_forward(u, x, nullptr);
+  lbm_status st = lbm_unet_forward(u, x, nullptr, 0);
   if (st) return st;
   const int lv = u->levels;
   const long P = (long)u->B * u->H * u->W;

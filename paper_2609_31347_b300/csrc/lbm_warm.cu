@@ -217,6 +217,89 @@ __global__ void k_decode(const float *__restrict__ y, int wc, int hc, int factor
   }
 }
 
+// Remove the Fourier components at the wavevectors (nx/2, 0) and (0, ny/2) (for even
+// sizes) of one population plane per block: sum_n (-1)^x f(n) / N and sum_n (-1)^y f(n) / N
+// are the coefficients of the two orthogonal sign patterns.  The primal and adjoint
+// steps have the eigenvalue -1 at those wavevectors, so error there would alternate
+// forever instead of decaying; the steady state of a smooth field has none.
+__global__ void __launch_bounds__(1024) k_drop_half_nyquist(double *__restrict__ pop, int nx,
+                                                             int ny) {
+  const long N = (long)nx * ny;
+  double *f = pop + (long)blockIdx.x * N;
+  double sx = 0.0, sy = 0.0;
+  for (long i = threadIdx.x; i < N; i += blockDim.x) {
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    const double v = f[i];
+    sx += (x & 1) ? -v : v;
+    sy += (y & 1) ? -v : v;
+  }
+  __shared__ double sm[2][1024];
+  sm[0][threadIdx.x] = sx;
+  sm[1][threadIdx.x] = sy;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + o];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const double ax = (nx % 2 == 0) ? sm[0][0] / (double)N : 0.0;
+  const double ay = (ny % 2 == 0) ? sm[1][0] / (double)N : 0.0;
+  for (long i = threadIdx.x; i < N; i += blockDim.x) {
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    f[i] -= ((x & 1) ? -ax : ax) + ((y & 1) ? -ay : ay);
+  }
+}
+
+// Set the conserved k = 0 components of one sample (block) to zero.  On the periodic
+// lattice the mean displacement is conserved by both iterations (the eigenvalue 1 at
+// k = 0, two collision invariants): from rest with a zero-mean force (source) it stays
+// zero, so a warm start must start there too, or the iteration settles on a rigidly
+// shifted state.  Primal (mode 1): the means of m10 = <c_x, f> and m01 = <c_y, f> are
+// removed along the stationary states v_x, v_y (m10 = 1 resp. m01 = 1, third-order
+// moments at equilibrium theta, all else 0).  Adjoint (mode 2): the conserved quantities
+// are <v_x, phi>, <v_y, phi>, removed along c_x, c_y (<v_x, c_x> = 1, <v_y, c_x> = 0).
+__global__ void __launch_bounds__(256) k_drop_conserved_mean(double *__restrict__ pop, long N,
+                                                              int mode) {
+  double *f = pop + (long)blockIdx.x * 8 * N;
+  double acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+  for (long n = threadIdx.x; n < N; n += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] += f[k * N + n];
+  __shared__ double sm[8][256];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  const double cx[8] = {1, 0, -1, 0, 1, -1, -1, 1}, cy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+  const double a = 0.5 * (1.0 - kTh), b = 0.25 * kTh;
+  const double vx[8] = {a, 0, -a, 0, b, -b, -b, b}, vy[8] = {0, a, 0, -a, b, b, -b, -b};
+  const double *wx = mode == 1 ? cx : vx, *wy = mode == 1 ? cy : vy;  // conserved functionals
+  const double *ux = mode == 1 ? vx : cx, *uy = mode == 1 ? vy : cy;  // removed along these
+  double ax = 0.0, ay = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    ax += wx[k] * sm[k][0];
+    ay += wy[k] * sm[k][0];
+  }
+  ax /= (double)N;
+  ay /= (double)N;
+  double d[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) d[k] = ax * ux[k] + ay * uy[k];
+  for (long n = threadIdx.x; n < N; n += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k * N + n] -= d[k];
+}
+
 // rms[i] = sqrt(mean over the first P' pixels of t[., i]^2), P' = min(P, 2^22); one
 // block per channel, fixed order.
 __global__ void __launch_bounds__(1024) k_channel_rms(const float *__restrict__ t, long P,
@@ -282,6 +365,11 @@ lbm_status lbm_warm_decode(int count, int wc, int hc, int factor, double dx_fine
   const long N = (long)wc * hc * factor * factor;
   k_decode<<<grid_for((long)count * N), 256, 0, (cudaStream_t)stream>>>(
       y_dev, wc, hc, factor, dx_fine, mode, scale_dev, chan_dev, pop_dev, count, accumulate);
+  if (mode != 0) {
+    k_drop_half_nyquist<<<count * 8, 1024, 0, (cudaStream_t)stream>>>(pop_dev, wc * factor,
+                                                                     hc * factor);
+    k_drop_conserved_mean<<<count, 256, 0, (cudaStream_t)stream>>>(pop_dev, N, mode);
+  }
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 

@@ -2,7 +2,9 @@
 
 - ``LBMObjective``: a ``torch.autograd.Function`` whose forward runs the primal solve
   and the objective (Algorithm 2, line 3) and whose backward runs the adjoint solve and
-  the gradient (Algorithm 1, Eq. optimality).  Only the steady primal state f_S is kept
+  the gradient (Algorithm 1, Eq. optimality).  A control at which the primal iteration
+  diverges (no steady state, e.g. a modulus that makes the boundary collision singular)
+  gets J = +inf, so that the line search steps back.  Only the steady primal state f_S is kept
   for the backward pass (the adjoint of a steady problem needs no trajectory); it is
   restored into the handle if another forward ran in between.
 - ``lbfgs``: limited-memory BFGS (two-loop recursion) with a line search satisfying the
@@ -15,10 +17,13 @@ dot products.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 from typing import Callable, List, Optional
 
 import torch
+
+from .lbm import LBM_ERR_DIVERGED
 
 
 @dataclass
@@ -47,11 +52,20 @@ class LBMObjective(torch.autograd.Function):
         solver.set_control(a)
         if warm is not None:
             warm.before_primal(solver, a)
-        solver.primal_solve(**primal.kw())
+        info = solver.primal_solve(**primal.kw())
+        ctx.solver, ctx.adjoint, ctx.project, ctx.warm = solver, adjoint, project, warm
+        ctx.failed = info.status == LBM_ERR_DIVERGED  # no steady state at this control
+        if ctx.failed:
+            # J = +inf makes the line search step back; the gradient is not used
+            ctx.alpha = alpha.detach().clone()
+            return alpha.new_tensor(float("inf"))
+        J = solver.objective()
+        if not math.isfinite(J):
+            ctx.failed = True
+            ctx.alpha = alpha.detach().clone()
+            return alpha.new_tensor(float("inf"))
         if warm is not None:
             warm.after_primal(solver, a)
-        J = solver.objective()
-        ctx.solver, ctx.adjoint, ctx.project, ctx.warm = solver, adjoint, project, warm
         ctx.fS = solver.get_populations(0).clone()  # steady-state checkpoint
         ctx.alpha = alpha.detach().clone()
         solver._state_token = id(ctx)
@@ -60,6 +74,8 @@ class LBMObjective(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gJ):
+        if ctx.failed:
+            return torch.zeros_like(ctx.alpha), None, None, None, None, None
         s = ctx.solver
         if getattr(s, "_state_token", None) != ctx.token:
             # another evaluation overwrote the handle: restore control and steady state
@@ -69,7 +85,9 @@ class LBMObjective(torch.autograd.Function):
             s._state_token = ctx.token
         if ctx.warm is not None:
             ctx.warm.before_adjoint(s)
-        s.adjoint_solve(**ctx.adjoint.kw())
+        info = s.adjoint_solve(**ctx.adjoint.kw())
+        if info.status == LBM_ERR_DIVERGED:
+            raise RuntimeError("adjoint solve diverged at a control whose primal converged")
         if ctx.warm is not None:
             ctx.warm.after_adjoint(s)
         g = s.gradient(project_zero_mean=ctx.project)
@@ -169,8 +187,11 @@ def strong_wolfe(fg, x, f0, g0, d, lam0=1.0, c1=1e-4, c2=0.9, kmax=100):
 def lbfgs(fg: Callable, alpha0: torch.Tensor, m_max: int = 50, eps: float = 1e-10,
           eps_alpha: float = 2.2e-16, history: int = 20, lam0: float = 1.0,
           gamma0: Optional[float] = None, k_max: int = 100,
-          norm: Optional[Callable] = None) -> LBFGSResult:
+          norm: Optional[Callable] = None, f_target: Optional[float] = None) -> LBFGSResult:
     """Minimise J with L-BFGS (Algorithm 2).  fg(alpha) -> (J, dJ/dalpha).
+
+    f_target (optional, not part of Algorithm 2): also stop once J <= f_target, to compare
+    runs by the work they need to reach the same objective.
 
     gamma0 scales the first step's direction (H0 = gamma0 I before any curvature pair;
     None: 1 / |g|_1); later steps use the usual s'y / y'y scaling.  norm(g) is the
@@ -186,6 +207,8 @@ def lbfgs(fg: Callable, alpha0: torch.Tensor, m_max: int = 50, eps: float = 1e-1
         gn = norm(g)
         if gn < eps:
             return LBFGSResult(x, f, gn, m, "gradient", hist)
+        if f_target is not None and f <= f_target:
+            return LBFGSResult(x, f, gn, m, "target", hist)
         # two-loop recursion: d = -H g
         q = g.clone()
         al = []
@@ -220,6 +243,8 @@ def lbfgs(fg: Callable, alpha0: torch.Tensor, m_max: int = 50, eps: float = 1e-1
         hist.append({"J": f, "grad_norm": norm(g), "step": a})
         if bool(torch.all(rel < eps_alpha)):
             return LBFGSResult(x, f, norm(g), m + 1, "control change", hist)
+    if f_target is not None and f <= f_target:
+        return LBFGSResult(x, f, norm(g), m_max, "target", hist)
     return LBFGSResult(x, f, norm(g), m_max, "m_max", hist)
 
 

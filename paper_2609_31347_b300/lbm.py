@@ -113,7 +113,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_unet_param_count": ([P], ctypes.c_long),
         "lbm_unet_get_params": ([P, P, I], I),
         "lbm_unet_set_params": ([P, P], I),
-        "lbm_unet_forward": ([P, P, P], I),
+        "lbm_unet_forward": ([P, P, P, I], I),
         "lbm_unet_train_step": ([P, P, P, ctypes.c_float, P], I),
         "lbm_solid_adjoint_source": ([P, P], I),
         "lbm_warm_encode": ([I, I, I, I, P, P, P, P, P], I),
@@ -168,6 +168,7 @@ class LBMSolid:
         import torch
         self._lib = load_library()
         self.nx, self.ny, self.N = int(nx), int(ny), int(nx) * int(ny)
+        self.dx, self.periodic = float(dx), bool(periodic)
         self.sweeps = {}  # sweeps performed per solve kind ("primal_solve", ...)
         self.control = control
         N = self.N
@@ -448,13 +449,14 @@ class UNet:
         self._check(self._lib.lbm_unet_set_params(self._h, self._f32(p, self.nparams)),
                     "set_params")
 
-    def forward(self, x, out=None):
+    def forward(self, x, out=None, exact_acts: bool = False):
+        """y = net(x); exact_acts: FP32 activations (split-BF16 products) instead of BF16."""
         import torch
         P = self.batch * self.H * self.W
         if out is None:
             out = torch.empty((self.batch, self.H, self.W, 8), dtype=torch.float32, device="cuda")
-        self._check(self._lib.lbm_unet_forward(self._h, self._f32(x, 2 * P), self._f32(out, 8 * P)),
-                    "forward")
+        self._check(self._lib.lbm_unet_forward(self._h, self._f32(x, 2 * P), self._f32(out, 8 * P),
+                                               1 if exact_acts else 0), "forward")
         return out
 
     def train_step(self, x, t, lr: float):

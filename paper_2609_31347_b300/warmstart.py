@@ -68,7 +68,7 @@ class WarmStartNet:
 
     # ---- data -------------------------------------------------------------------
     def generate(self, count: int, sweeps: int, seed: int = 1, chunk: int = 256,
-                 modes: int = 8, kmax: int = 8):
+                 modes: int = 8, kmax: int = 4):
         """`count` (input, target) pairs from the solver: random smooth fields (``modes``
         Fourier modes, |k| up to kmax * 2 pi) drive a batch of lattices for `sweeps`
         sweeps from rest.  Returns device tensors X (count, nx, nx, 2) and
@@ -139,13 +139,14 @@ class WarmStartNet:
         return log
 
     def evaluate(self, X, T):
-        """Relative L2 error of the predictions over a data set (full batches)."""
+        """Relative L2 error of the predictions (FP32 activations, as used for warm starts)
+        over a data set (full batches)."""
         import torch
         B = self.batch
         num = den = 0.0
         out = torch.empty((B,) + tuple(T.shape[1:]), dtype=torch.float32, device="cuda")
         for j in range(X.shape[0] // B):
-            self.net.forward(X[j * B:(j + 1) * B], out)
+            self.net.forward(X[j * B:(j + 1) * B], out, exact_acts=True)
             t = T[j * B:(j + 1) * B]
             num += float(torch.sum((out.double() - t.double()) ** 2))
             den += float(torch.sum(t.double() ** 2))
@@ -174,7 +175,7 @@ class WarmStartNet:
         net = self._inference_net()
         self._check(self._lib.lbm_warm_encode(1, nxf, nxf, factor, _ptr(field), _ptr(ref),
                                               _ptr(self._x), _ptr(self._s), self._st()), "encode")
-        net.forward(self._x, self._y)
+        net.forward(self._x, self._y, exact_acts=True)
         self._check(self._lib.lbm_warm_decode(1, self.nx, self.nx, factor, dxf, self.mode,
                                               _ptr(self._y), _ptr(self._s), _ptr(self.chan),
                                               _ptr(out), 1 if accumulate else 0, self._st()),

@@ -1,7 +1,8 @@
 """GPU warm-start network (BF16 storage, FP32 accumulation on the tensor cores) against
 the FP64 CPU reference in oracle/unet.py: forward output, loss and every parameter
-gradient, for the configured 4-level, 32-channel network and for smaller shapes; and
-training by the library's own kernels lowers the loss.
+gradient, for the configured 4-level, 32-channel network and for smaller shapes; the
+FP32-activation forward used for warm starts against the reference with BF16-rounded
+weights; and training by the library's own kernels lowers the loss.
 
 Tolerance: activations are rounded to BF16 (relative 2^-9) after each of about twenty
 layers and the products are BF16 x BF16 with FP32 sums, so the outputs and gradients
@@ -74,6 +75,39 @@ def test_forward_and_gradients_match_cpu_reference(lbm, base, levels, B, H, W):
     assert np.array_equal(net.params(0).cpu().numpy().astype(np.float64),
                           np.concatenate([np.concatenate([pr[n + ".w"].ravel(), pr[n + ".b"]])
                                           for n, *_ in shapes]))
+    net.close()
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("base,levels,B,H,W", [(32, 4, 1, 128, 128), (16, 2, 2, 32, 64)])
+def test_exact_activation_forward_is_the_bf16_weight_network(lbm, base, levels, B, H, W):
+    # FP32 activations with split-BF16 products: the map of the BF16-rounded weights up
+    # to FP32 sums (relative error ~1e-5), against the FP64 reference with those weights
+    net = lbm.UNet(B, H, W, base=base, levels=levels, seed=4)
+    shapes = U.layer_shapes(base=base, levels=levels)
+    rng = np.random.default_rng(9)
+    p = net.params(0).cpu().numpy().astype(np.float64)
+    pr = unflatten(p.copy(), shapes)
+    for name, _, _, co in shapes:
+        pr[name + ".b"][:] = 0.1 * rng.standard_normal(co)
+    p = np.concatenate([np.concatenate([pr[n + ".w"].ravel(), pr[n + ".b"]]) for n, *_ in shapes])
+    net.set_params(torch.as_tensor(p.astype(np.float32), device="cuda"))
+    pr = unflatten(net.params(0).cpu().numpy().astype(np.float64), shapes)
+    for n, *_ in shapes:
+        pr[n + ".w"] = bf16(pr[n + ".w"])
+    x = rng.standard_normal((B, H, W, 2)).astype(np.float32)
+    y = net.forward(torch.as_tensor(x, device="cuda"), exact_acts=True).cpu().numpy()
+    yref = U.forward(pr, x.astype(np.float64), levels=levels)
+    assert rel(y, yref) < 1e-4, rel(y, yref)
+    # BF16 activations are ~100x further off
+    yb = net.forward(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    assert rel(yb, yref) > 10 * rel(y, yref)
     net.close()
 
 

@@ -1,6 +1,7 @@
 """Pins of the warm-start network's CPU reference (oracle/unet.py), CPU only:
-convolution of a delta is the (flipped) kernel, translation equivariance by multiples of
-the coarsest cell, linearity, and backward = finite differences of forward."""
+convolution of a delta is the (flipped) kernel, bilinear upsampling reproduces linear
+functions, translation equivariance by multiples of the coarsest cell, linearity, and
+backward = finite differences of forward."""
 import numpy as np
 
 from oracle import unet
@@ -17,6 +18,26 @@ def test_conv_of_a_delta_is_the_kernel():
         for dx in (-1, 0, 1):
             assert np.allclose(y[0, 4 - dy, 5 - dx], w[dy + 1, dx + 1, 1])
     assert np.count_nonzero(np.abs(y) > 0) == 9 * 3
+
+
+def test_upsampling_is_bilinear():
+    # coarse cell j is the centre of fine cells 2j, 2j+1 (position 2j + 1/2): sampling a
+    # linear function there, the upsampled values are that function at the fine cells
+    # (away from the periodic seam), and constants stay constant
+    H = W = 8
+    jy, jx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    f = lambda y, x: 0.3 + 1.7 * y - 0.9 * x + 0.2 * x * y  # bilinear
+    c = f(2 * jy + 0.5, 2 * jx + 0.5)[None, :, :, None]
+    u = unet.up(c)[0, :, :, 0]
+    iy, ix = np.meshgrid(np.arange(2 * H), np.arange(2 * W), indexing="ij")
+    inner = (iy >= 1) & (iy <= 2 * H - 2) & (ix >= 1) & (ix <= 2 * W - 2)
+    assert np.allclose(u[inner], f(iy, ix)[inner], atol=1e-12)
+    assert np.allclose(unet.up(np.full((1, 4, 4, 3), 2.5)), 2.5)
+    # the backward is the transpose
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 4, 6, 3))
+    y = rng.standard_normal((2, 8, 12, 3))
+    assert np.isclose(np.sum(unet.up(x) * y), np.sum(x * unet.up_backward(y)), rtol=1e-13)
 
 
 def test_network_is_linear_plus_bias_and_translation_equivariant():
@@ -54,4 +75,6 @@ def test_backward_matches_finite_differences():
         Lm = unet.mse_loss(unet.forward(p, x), t)[0]
         p[name][idx] = old
         fd = (Lp - Lm) / (2 * h)
-        assert abs(fd - grads[name][idx]) <= 1e-6 * max(abs(fd), 1e-8), (name, fd, grads[name][idx])
+        # central differences of a quadratic: only cancellation, ~ eps L / h
+        assert abs(fd - grads[name][idx]) <= 1e-6 * abs(fd) + 1e-9 * max(L, 1.0), \
+            (name, fd, grads[name][idx])
