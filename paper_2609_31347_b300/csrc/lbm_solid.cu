@@ -569,6 +569,13 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
   while (bx > 32 && bx / 2 >= (unsigned)d->nx) bx /= 2;
   h->blk = dim3(bx, 256 / bx);
   h->grd = dim3((d->nx + h->blk.x - 1) / h->blk.x, (d->ny + h->blk.y - 1) / h->blk.y);
+  // small lattices are latency-bound: smaller blocks spread the nodes (and the FP64
+  // boundary nodes) over more of the 148 SMs
+  while ((long)h->grd.x * h->grd.y < 148 && h->blk.x * h->blk.y > 64) {
+    if (h->blk.y > 1) h->blk.y /= 2;
+    else h->blk.x /= 2;
+    h->grd = dim3((d->nx + h->blk.x - 1) / h->blk.x, (d->ny + h->blk.y - 1) / h->blk.y);
+  }
   h->nblocks2d = (long)h->grd.x * h->grd.y;
   h->partial_cap = 4 * (h->nblocks2d > 148 * 8 ? h->nblocks2d : 148 * 8);
   cudaError_t e = cudaSuccess;

@@ -124,19 +124,23 @@ def fourier_force(nx: int, modes: int = 8, kmax: int = 4, seed: int = 1, ny: Opt
 
 
 def fourier_fields(count: int, nx: int, seed: int, modes: int = 8, kmax: int = 8,
-                   unit_norm: bool = False, device: str = "cuda"):
+                   unit_norm: bool = False, exponents=(1.0,), device: str = "cuda"):
     """`count` random zero-mean two-component fields on the periodic nx^2 grid, as a
     (count, 2, nx*nx) float64 torch tensor on `device` (the layout of a batch of equal
     lattices).  Each field is `modes` Fourier modes with wavevectors 2 pi (kx, ky),
-    kx, ky in {-kmax..kmax} not both zero, and N(0, 1/|k|^2) sin/cos amplitudes per
-    component (smoother fields have more weight, as do the steady states they drive).
-    unit_norm scales every field to Euclidean norm 1 over its 2N values."""
+    kx, ky in {-kmax..kmax} not both zero, and N(0, |k|^(-2p)) sin/cos amplitudes per
+    component, the spectral exponent p drawn per field from `exponents` (p = 1: force-like
+    fields; p = 3: displacement-like fields, as the response to a p = 1 force decays by
+    two more powers).  unit_norm scales every field to Euclidean norm 1 over its 2N
+    values."""
     import torch
     rng = np.random.default_rng(seed)
     k = rng.integers(-kmax, kmax + 1, size=(count, modes, 2))
     zero = (k[..., 0] == 0) & (k[..., 1] == 0)
     k[zero, 0] = 1
-    amp = rng.standard_normal((count, modes, 4)) / np.hypot(k[..., 0], k[..., 1])[..., None]
+    p = rng.choice(np.asarray(exponents, dtype=float), size=(count, 1))
+    amp = rng.standard_normal((count, modes, 4)) * \
+        (np.hypot(k[..., 0], k[..., 1]) ** -p)[..., None]
     x = torch.arange(nx, dtype=torch.float64, device=device) / nx
     Y, X = torch.meshgrid(x, x, indexing="ij")
     kt = torch.as_tensor(k, dtype=torch.float64, device=device)

@@ -68,11 +68,12 @@ class WarmStartNet:
 
     # ---- data -------------------------------------------------------------------
     def generate(self, count: int, sweeps: int, seed: int = 1, chunk: int = 256,
-                 modes: int = 8, kmax: int = 4):
+                 modes: int = 8, kmax: int = 4, exponents=(1.0, 2.0, 3.0)):
         """`count` (input, target) pairs from the solver: random smooth fields (``modes``
-        Fourier modes, |k| up to kmax * 2 pi) drive a batch of lattices for `sweeps`
-        sweeps from rest.  Returns device tensors X (count, nx, nx, 2) and
-        T (count, nx, nx, 8), FP32."""
+        Fourier modes, |k| up to kmax * 2 pi, amplitude spectra |k|^-p with p drawn from
+        `exponents`, from force-like to displacement-like inputs) drive a batch of
+        lattices for `sweeps` sweeps from rest.  Returns device tensors
+        X (count, nx, nx, 2) and T (count, nx, nx, 8), FP32."""
         import torch
         nx, N = self.nx, self.nx * self.nx
         X = torch.empty((count, nx, nx, 2), dtype=torch.float32, device="cuda")
@@ -81,7 +82,8 @@ class WarmStartNet:
         for start in range(0, count, chunk):
             m = min(chunk, count - start)
             fields = I.fourier_fields(m, nx, seed=seed * 1_000_003 + start, modes=modes,
-                                      kmax=kmax, unit_norm=self.kind == "adjoint")
+                                      kmax=kmax, unit_norm=self.kind == "adjoint",
+                                      exponents=exponents)
             b = L.LBMBatch([(nx, nx)] * m, self.E, self.nu, dx=[self.dx] * m, stream=self.stream)
             if self.kind == "primal":
                 b.set_force(fields.reshape(-1))
@@ -187,13 +189,21 @@ class WarmStarter:
     """Initial states for the solves of an optimisation loop over a FORCE_FIELD control.
 
     primal / adjoint: trained ``WarmStartNet`` or None.  reuse: start from the previous
-    steady state (plus the network's state of the change, when there is a network).
-    With neither a network nor reuse every solve starts from rest, as in the paper."""
+    steady state.  For the primal with both, the network's state of the control change
+    is added to the previous state.  For the adjoint with reuse, the previous state is
+    used alone unless ``adjoint_change`` is set: measured over an L-BFGS run on the 512^2
+    lattice, adding the network's state of the change of r cost more adjoint sweeps than
+    reusing the previous state alone, while on a single solve without a previous state
+    the adjoint network saved 20-30 % of the sweeps.  With neither a network nor reuse
+    every solve starts from rest, as in the paper."""
 
     def __init__(self, primal: Optional[WarmStartNet] = None,
-                 adjoint: Optional[WarmStartNet] = None, reuse: bool = True):
+                 adjoint: Optional[WarmStartNet] = None, reuse: bool = True,
+                 adjoint_change: bool = False):
         self.primal, self.adjoint, self.reuse = primal, adjoint, reuse
+        self.adjoint_change = adjoint_change
         self.F_prev = self.f_prev = self.r_prev = self.p_prev = None
+        self._r = None
 
     def before_primal(self, solver, F):
         if self.primal is None and not (self.reuse and self.f_prev is not None):
@@ -215,24 +225,25 @@ class WarmStarter:
             self.f_prev = solver.get_populations(0).clone()
 
     def before_adjoint(self, solver):
-        if self.adjoint is None and not (self.reuse and self.p_prev is not None):
+        have_prev = self.reuse and self.p_prev is not None
+        if self.adjoint is None and not have_prev:
             return
-        r = solver.adjoint_source()
-        if self.reuse and self.p_prev is not None:
+        if have_prev:
             p0 = self.p_prev.clone()
-            if self.adjoint is not None:
-                self.adjoint.predict(r, p0, ref=self.r_prev, accumulate=True)
+            if self.adjoint is not None and self.adjoint_change:
+                self._r = solver.adjoint_source()
+                self.adjoint.predict(self._r, p0, nx_fine=solver.nx, dx_fine=solver.dx,
+                                     ref=self.r_prev, accumulate=True)
         else:
             import torch
+            self._r = solver.adjoint_source()
             p0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
-            self.adjoint.predict(r, p0)
+            self.adjoint.predict(self._r, p0, nx_fine=solver.nx, dx_fine=solver.dx)
         solver.set_populations(2, p0)
-        self._r = r
 
     def after_adjoint(self, solver):
         if self.reuse:
-            self.r_prev = getattr(self, "_r", None)
-            if self.r_prev is None:
-                self.r_prev = solver.adjoint_source()
+            if self.adjoint is not None and self.adjoint_change:
+                self.r_prev = self._r if self._r is not None else solver.adjoint_source()
             self.p_prev = solver.get_populations(2).clone()
-            self._r = None
+        self._r = None
