@@ -114,13 +114,17 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SWEEP_SOURCES = ("lbm_boundary.cuh", "lbm_device.cuh", "lbm_fixed.cuh", "lbm_kernels.cuh",
+                 "lbm_solid.cu")  # the single-lattice sweep kernels and their launches
+
+
 def csrc_digest():
-    """sha256 over the CUDA sources (sorted file names), to tie a stored ncu figure to the
-    exact kernel code it was taken on."""
+    """sha256 over the sources of the single-lattice sweep kernels and their launch
+    configuration, to tie a stored ncu figure to the exact code it was taken on."""
     import hashlib
     d = os.path.join(ROOT, "paper_2609_31347_b300", "csrc")
     h = hashlib.sha256()
-    for p in sorted(os.listdir(d)):
+    for p in SWEEP_SOURCES:
         with open(os.path.join(d, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
