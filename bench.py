@@ -177,13 +177,25 @@ def time_to_gradient(torch, lbm, I, reps: int = 3):
     s.set_target(torch.as_tensor(c["dstar"].ravel(), device="cuda"))
     out["amplitudes_32"] = timed(s, torch.tensor([0.5, 0.25], dtype=torch.float64, device="cuda"), 2)
     s.close()
-    # distributed force control, 80^2 (12,800 controls), at half the reference force
-    c = I.config_amplitudes(80)
-    F = 0.5 * np.tensordot([1.0, 0.5], c["basis"], axes=1)
-    s = lbm.LBMSolid(80, 80, c["dx"], c["E"], c["nu"], control="force_field")
-    s.set_target(torch.as_tensor(c["dstar"].ravel(), device="cuda"))
-    out["force_field_80"] = timed(s, torch.as_tensor(F.ravel(), device="cuda"), 12800)
-    s.close()
+    # distributed force control at half the reference force; 80^2 = 12,800 controls is the
+    # task's configuration, the others are the resolution ladder
+    for n in (20, 40, 80, 160):
+        c = I.config_amplitudes(n)
+        F = 0.5 * np.tensordot([1.0, 0.5], c["basis"], axes=1)
+        s = lbm.LBMSolid(n, n, c["dx"], c["E"], c["nu"], control="force_field")
+        s.set_target(torch.as_tensor(c["dstar"].ravel(), device="cuda"))
+        out["force_field_%d" % n] = timed(s, torch.as_tensor(F.ravel(), device="cuda"), 2 * n * n)
+        s.close()
+    # benchmark (1): alpha o F* on the periodic manufactured solution, N_x = 10 .. 80, at
+    # alpha = (-0.5, -0.5) (the optimum is alpha = -1)
+    for n in (10, 20, 40, 80):
+        m = I.periodic_manufactured(n)
+        s = lbm.LBMSolid(n, n, m["dx"], I.PAPER_E, I.PAPER_NU, control="force_basis2",
+                         force_basis=I.paper_scale_basis(m["Fstar"]).reshape(-1))
+        s.set_target(torch.as_tensor(m["dstar"].ravel(), device="cuda"))
+        out["benchmark1_%d" % n] = timed(s, torch.tensor([-0.5, -0.5], dtype=torch.float64,
+                                                          device="cuda"), 2)
+        s.close()
     # elliptic plate, N_x = 64, scalar Young's modulus at E = 0.15 (E* = 0.1)
     geo = I.plate_geometry(64)
     dstar, sigma, Fp = I.plate_manufactured(geo.X, geo.Y)

@@ -237,7 +237,9 @@ lbm_status lbm_batch_tune(lbm_batch *b, int sweeps, int *best_bx);
  * levels; decoder: bilinear 2x upsampling (periodic, coarse values at the centres of
  * their 2x2 blocks), concatenation [upsampled, skip], two 3x3
  * convolutions; a 1x1 head to 8 channels.  Input 2 channels, output 8.  BF16 weights
- * and activations, FP32 accumulation on the tensor cores, FP32 master weights and Adam.
+ * and activations, FP32 accumulation on the tensor cores (3x3 convolutions: tcgen05.mma
+ * with the accumulator in tensor memory; 1x1 head and weight gradients: mma.sync), FP32
+ * master weights and Adam.
  *
  * Layout: x (B, H, W, 2) and y, t (B, H, W, 8) FP32 NHWC device arrays borrowed for
  * the call; parameters are one FP32 vector, per layer in execution order (encoder
@@ -254,6 +256,9 @@ lbm_status lbm_unet_create(int base, int levels, int batch, int H, int W,
                            unsigned long long seed, void *stream, lbm_unet **out);
 lbm_status lbm_unet_destroy(lbm_unet *u);
 long lbm_unet_param_count(const lbm_unet *u); /* -1 for NULL */
+/* Synchronises the stream; LBM_ERR_CUDA if a tensor-core convolution of this network
+   gave up waiting for its own matrix operations (its outputs were then set to NaN). */
+lbm_status lbm_unet_status(lbm_unet *u);
 /* Copies the parameter vector (which = 0) or the last gradient (which = 1) into dst. */
 lbm_status lbm_unet_get_params(lbm_unet *u, float *dst_dev, int which);
 /* Replaces the parameter vector (Adam moments are kept). */

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "lbm_solid.h"
+#include "lbm_unet_tc.cuh"
 
 namespace {
 
@@ -417,6 +418,7 @@ struct lbm_unet {
   // FP32 activations of the exact-activation forward (allocated on first use)
   float *x32 = nullptr;
   std::vector<float *> out32, pooled32, upcat32;
+  int *err = nullptr;  // set by a tensor-core convolution whose wait timed out
   long step = 0;
   std::vector<void *> allocs;
 };
@@ -436,15 +438,40 @@ T *dalloc(lbm_unet *u, size_t n, cudaError_t &e) {
 
 unsigned gs(long n) { long b = (n + 255) / 256; return (unsigned)(b < 148 * 16 ? (b < 1 ? 1 : b) : 148 * 16); }
 
+// 3x3 convolution on the tensor cores (tcgen05, accumulator in TMEM): Kc-channel chunks
+// (64, 32 or 16, dividing Cin), N-tiles of up to 256 output channels (384 = 2 x 192).
+template <typename TIN>
+void conv3_tc(lbm_unet *u, const TIN *in, int Cin, const bf16 *w, int Cout, const float *bias,
+              bf16 *out_bf, float *out_f, int Hh, int Ww, int sgn) {
+  const int kc = Cin % 64 == 0 ? 64 : (Cin % 32 == 0 ? 32 : 16);
+  const int nt = Cout <= 256 ? Cout : (Cout % 192 == 0 ? 192 : 128);
+  int tcols = 32;
+  while (tcols < nt) tcols *= 2;
+  const bool split = sizeof(TIN) == 4;
+  size_t smem = 2 * ((size_t)tc::kM * kc * 2 * (split ? 2 : 1) + (size_t)nt * kc * 2);
+  // at most 512 / tcols CTAs per SM, so that their TMEM allocations always fit
+  if (smem < (size_t)tcols * 456) smem = (size_t)tcols * 456;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::k_conv3<TIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const long P = (long)u->B * Hh * Ww;
+  dim3 grid((unsigned)((P + tc::kM - 1) / tc::kM), (unsigned)(Cout / nt));
+  tc::k_conv3<TIN><<<grid, tc::kThreads, smem, u->stream>>>(in, Cin, w, Cout, bias, out_bf, out_f,
+                                                           u->B, Hh, Ww, sgn, kc, nt, tcols, u->err);
+}
+
 template <typename TIN>
 void conv_fwd(lbm_unet *u, const Layer &l, const TIN *in, bf16 *out_bf, float *out_f, int Hh, int Ww) {
+  const float *bias = u->p + l.boff;
+  if (l.ks == 3) {
+    conv3_tc<TIN>(u, in, l.cipad, l.wf, l.co, bias, out_bf, out_f, Hh, Ww, 1);
+    return;
+  }
   const long tiles = (long)u->B * Hh * (Ww / 16);
   dim3 grid((unsigned)((tiles + 3) / 4), (unsigned)((l.co + 31) / 32));
-  const float *bias = u->p + l.boff;
-  if (l.ks == 3)
-    k_conv<3, TIN><<<grid, 128, 0, u->stream>>>(in, l.cipad, l.wf, l.co, bias, out_bf, out_f, u->B, Hh, Ww, 1);
-  else
-    k_conv<1, TIN><<<grid, 128, 0, u->stream>>>(in, l.cipad, l.wf, l.co, bias, out_bf, out_f, u->B, Hh, Ww, 1);
+  k_conv<1, TIN><<<grid, 128, 0, u->stream>>>(in, l.cipad, l.wf, l.co, bias, out_bf, out_f, u->B, Hh, Ww, 1);
 }
 
 // a layer's output in the activation type of the pass
@@ -507,7 +534,7 @@ void conv_bwd(lbm_unet *u, Layer &l, const bf16 *gout, int Hh, int Ww, bool need
     const long tiles = P / 16;
     dim3 grid((unsigned)((tiles + 3) / 4), (unsigned)((l.cipad + 31) / 32));
     if (l.ks == 3)
-      k_conv<3, bf16><<<grid, 128, 0, u->stream>>>(gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, u->B, Hh, Ww, -1);
+      conv3_tc<bf16>(u, gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, Hh, Ww, -1);
     else
       k_conv<1, bf16><<<grid, 128, 0, u->stream>>>(gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, u->B, Hh, Ww, -1);
   }
@@ -566,6 +593,7 @@ lbm_status lbm_unet_create(int base, int levels, int batch, int H, int W, unsign
   u->v = dalloc<float>(u, u->nparams, e);
   const long P = (long)batch * H * W;
   u->y = dalloc<float>(u, P * 8, e);
+  u->err = dalloc<int>(u, 1, e);
   u->partial = dalloc<float>(u, 148 * 16, e);
   u->x16 = dalloc<bf16>(u, P * 16, e);
   u->gy = dalloc<bf16>(u, P * 16, e);
@@ -621,6 +649,15 @@ lbm_status lbm_unet_destroy(lbm_unet *u) {
 }
 
 long lbm_unet_param_count(const lbm_unet *u) { return u ? u->nparams : -1; }
+
+lbm_status lbm_unet_status(lbm_unet *u) {
+  if (!u) return LBM_ERR_ARG;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, u->err, sizeof(int), cudaMemcpyDeviceToHost, u->stream) != cudaSuccess ||
+      cudaStreamSynchronize(u->stream) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  return h ? LBM_ERR_CUDA : LBM_OK;
+}
 
 lbm_status lbm_unet_get_params(lbm_unet *u, float *dst, int which) {
   if (!u || !dst) return LBM_ERR_ARG;

@@ -34,7 +34,7 @@ EXPORTED = [
     "lbm_batch_set_target", "lbm_batch_primal", "lbm_batch_objective", "lbm_batch_adjoint",
     "lbm_batch_gradient", "lbm_batch_get_populations", "lbm_batch_tune", "lbm_solid_tangent",
     "lbm_unet_create", "lbm_unet_destroy", "lbm_unet_param_count", "lbm_unet_get_params",
-    "lbm_unet_set_params", "lbm_unet_forward", "lbm_unet_train_step",
+    "lbm_unet_set_params", "lbm_unet_forward", "lbm_unet_train_step", "lbm_unet_status",
     "lbm_solid_adjoint_source", "lbm_warm_encode", "lbm_warm_targets", "lbm_warm_decode", "lbm_warm_channel_rms",
 ]
 
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_unet_param_count": ([P], ctypes.c_long),
         "lbm_unet_get_params": ([P, P, I], I),
         "lbm_unet_set_params": ([P, P], I),
+        "lbm_unet_status": ([P], I),
         "lbm_unet_forward": ([P, P, P, I], I),
         "lbm_unet_train_step": ([P, P, P, ctypes.c_float, P], I),
         "lbm_solid_adjoint_source": ([P, P], I),
@@ -436,6 +437,10 @@ class UNet:
     def _f32(self, t, n):
         import torch
         return _dev_ptr(t, n, torch.float32)
+
+    def status(self):
+        """Synchronise; raise if a tensor-core convolution gave up waiting."""
+        self._check(self._lib.lbm_unet_status(self._h), "unet")
 
     def params(self, which: int = 0):
         """Copy of the FP32 parameter vector (0) or of the last gradient (1)."""

@@ -71,6 +71,7 @@ def test_forward_and_gradients_match_cpu_reference(lbm, base, levels, B, H, W):
         for part in (".w", ".b"):
             e = rel(g[name + part], gref[name + part])
             assert e < 5e-2, (name + part, e)
+    net.status()
     # lr = 0 leaves the parameters alone
     assert np.array_equal(net.params(0).cpu().numpy().astype(np.float64),
                           np.concatenate([np.concatenate([pr[n + ".w"].ravel(), pr[n + ".b"]])
@@ -104,6 +105,7 @@ def test_exact_activation_forward_is_the_bf16_weight_network(lbm, base, levels, 
     x = rng.standard_normal((B, H, W, 2)).astype(np.float32)
     y = net.forward(torch.as_tensor(x, device="cuda"), exact_acts=True).cpu().numpy()
     yref = U.forward(pr, x.astype(np.float64), levels=levels)
+    net.status()
     assert rel(y, yref) < 1e-4, rel(y, yref)
     # BF16 activations are ~100x further off
     yb = net.forward(torch.as_tensor(x, device="cuda")).cpu().numpy()
