@@ -444,7 +444,11 @@ template <typename TIN>
 void conv3_tc(lbm_unet *u, const TIN *in, int Cin, const bf16 *w, int Cout, const float *bias,
               bf16 *out_bf, float *out_f, int Hh, int Ww, int sgn) {
   const int kc = Cin % 64 == 0 ? 64 : (Cin % 32 == 0 ? 32 : 16);
-  const int nt = Cout <= 256 ? Cout : (Cout % 192 == 0 ? 192 : 128);
+  int nt = Cout <= 256 ? Cout : (Cout % 192 == 0 ? 192 : 128);
+  const long P = (long)u->B * Hh * Ww;
+  const long mt = (P + tc::kM - 1) / tc::kM;
+  // coarse levels have few pixels: narrower N-tiles put more CTAs on the 148 SMs
+  while (mt * (Cout / nt) < 148 && nt % 32 == 0 && Cout % (nt / 2) == 0) nt /= 2;
   int tcols = 32;
   while (tcols < nt) tcols *= 2;
   const bool split = sizeof(TIN) == 4;
@@ -456,8 +460,7 @@ void conv3_tc(lbm_unet *u, const TIN *in, int Cin, const bf16 *w, int Cout, cons
     cudaFuncSetAttribute(tc::k_conv3<TIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  const long P = (long)u->B * Hh * Ww;
-  dim3 grid((unsigned)((P + tc::kM - 1) / tc::kM), (unsigned)(Cout / nt));
+  dim3 grid((unsigned)mt, (unsigned)(Cout / nt));
   tc::k_conv3<TIN><<<grid, tc::kThreads, smem, u->stream>>>(in, Cin, w, Cout, bias, out_bf, out_f,
                                                            u->B, Hh, Ww, sgn, kc, nt, tcols, u->err);
 }

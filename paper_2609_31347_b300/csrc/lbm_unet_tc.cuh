@@ -11,8 +11,8 @@
 // into shared memory (cp.async, 16 B per copy; FP32 activations are split into high and
 // low BF16 parts on the way, two A tiles, two MMAs), in the no-swizzle K-major layout of
 // 8-row x 16-byte core matrices; one thread issues Kc/16 tcgen05.mma (kind::f16, BF16
-// inputs, FP32 accumulation) per chunk and commits them to the chunk's mbarrier, so the
-// next chunk's copies overlap the tensor-core work (two buffers).  The epilogue reads the
+// inputs, FP32 accumulation) per chunk and commits them to the buffer's mbarrier.  Two
+// buffers: the copies of chunk i + 1 are in flight while chunk i is multiplied.  The epilogue reads the
 // accumulator with tcgen05.ld (warp w: lanes 32w..32w+31), adds the bias and stores
 // BF16 or FP32 rows.
 //
@@ -131,33 +131,44 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
   const int iters = 9 * ksteps;
   const uint32_t id = idesc(nt);
   bool ok = true;
-  for (int it = 0; it < iters; ++it) {
-    const int buf = it & 1;
-    // the MMAs that read this buffer two chunks ago must be done (block-uniform decision)
-    const bool w_ok = it < 2 || wait_bar(&bar[buf], (uint32_t)(((it - 2) >> 1) & 1));
-    if (!__syncthreads_and(w_ok)) {
-      ok = false;
-      break;
+  // the pixel (b, y, x) of each A row this thread copies: rows q / cpr for
+  // q = tid, tid + 128, ... (at most 8 of them); -1 = beyond the last pixel
+  constexpr int kMaxRows = kM * 8 / kThreads;
+  long rb[kMaxRows];
+  int ry[kMaxRows], rx[kMaxRows];
+#pragma unroll
+  for (int i = 0; i < kMaxRows; ++i) {
+    const int q = tid + i * kThreads;
+    const long p = p0 + q / cpr;
+    rb[i] = -1;
+    ry[i] = rx[i] = 0;
+    if (q < kM * cpr && p < P) {
+      rx[i] = (int)(p % W);
+      const long t = p / W;
+      ry[i] = (int)(t % H);
+      rb[i] = (t / H) * H;
     }
+  }
+  // stage the operands of K-chunk `it` into buffer it & 1
+  auto load = [&](int it) {
+    const int buf = it & 1;
     const int tap = it / ksteps, k0 = (it % ksteps) * kc;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     const uint32_t abase = sbase + buf * buf_bytes;
     const uint32_t bbase = abase + a_bytes * (kSplit ? 2 : 1);
     // A: kM rows x kc channels of the shifted pixels
-    for (int q = tid; q < kM * cpr; q += kThreads) {
+#pragma unroll
+    for (int i = 0; i < kMaxRows; ++i) {
+      const int q = tid + i * kThreads;
+      if (q >= kM * cpr) break;
       const int r = q / cpr, c8 = q - r * cpr;
-      const long p = p0 + r;
-      const bool valid = p < P;
+      const bool valid = rb[i] >= 0;
       long src = 0;
       if (valid) {
-        const int x = (int)(p % W);
-        const long t = p / W;
-        const int y = (int)(t % H);
-        const long b = t / H;
-        int ys = y + sgn * dy, xs = x + sgn * dx;
+        int ys = ry[i] + sgn * dy, xs = rx[i] + sgn * dx;
         ys = ys < 0 ? ys + H : (ys >= H ? ys - H : ys);
         xs = xs < 0 ? xs + W : (xs >= W ? xs - W : xs);
-        src = ((b * H + ys) * W + xs) * Cin + k0 + c8 * 8;
+        src = ((rb[i] + ys) * W + xs) * Cin + k0 + c8 * 8;
       }
       const uint32_t off = tile_off(r, c8, kc);
       if (!kSplit) {
@@ -194,10 +205,27 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
       cp16(bbase + tile_off(n, c8, kc), wt + (long)n * Cin + c8 * 8, true);
     }
     asm volatile("cp.async.commit_group;");
-    asm volatile("cp.async.wait_group 0;");
+  };
+  load(0);
+  for (int it = 0; it < iters; ++it) {
+    // prefetch chunk it + 1 into the other buffer once the MMAs of chunk it - 1, which
+    // read it, are done (block-uniform decision)
+    if (it + 1 < iters) {
+      const bool w_ok = it < 1 || wait_bar(&bar[(it + 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
+      if (!__syncthreads_and(w_ok)) {
+        ok = false;
+        break;
+      }
+      load(it + 1);
+      asm volatile("cp.async.wait_group 1;");  // chunk it has landed, it + 1 may be in flight
+    } else {
+      asm volatile("cp.async.wait_group 0;");
+    }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
+      const uint32_t abase = sbase + (it & 1) * buf_bytes;
+      const uint32_t bbase = abase + a_bytes * (kSplit ? 2 : 1);
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t sbo = (uint32_t)kc * 16;
       for (int j = 0; j < kc / 16; ++j) {
@@ -205,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
         mma(tmem, sdesc(abase + j * 256, 128, sbo), bd, id, (it > 0 || j > 0) ? 1u : 0u);
         if (kSplit) mma(tmem, sdesc(abase + a_bytes + j * 256, 128, sbo), bd, id, 1u);
       }
-      commit(&bar[buf]);
+      commit(&bar[it & 1]);
     }
   }
   // the last commit covers every MMA issued before it
