@@ -113,6 +113,24 @@ def test_half_nyquist_force_is_never_damped(axis):
     assert np.abs(b - a).max() <= 1e-13 * np.abs(b).max()
 
 
+def test_states_are_linear_in_the_force_and_the_tangent_is_a_primal():
+    # From f_S(0) = 0 the periodic step is linear in the force (Section 3.1: affine
+    # collision, permutation streaming), so the state after T steps for a1 F1 + a2 F2 is
+    # a1 f(F1) + a2 f(F2), and the forward-mode tangent along a force direction Fd (at
+    # any F, the modulus fixed) is the primal state driven by Fd alone.
+    nx, T = 10, 150
+    g = oracle.Grid(nx, nx, 1.0 / nx, 1.0 / 3.0)
+    E = 8.0 / 3.0
+    F1 = I.fourier_force(nx, seed=11, kmax=3)
+    F2 = I.fourier_force(nx, seed=12, kmax=3)
+    f1, f2 = oracle.primal(g, E, F1, T), oracle.primal(g, E, F2, T)
+    f12 = oracle.primal(g, E, 0.7 * F1 - 1.3 * F2, T)
+    scale = np.abs(f12).max()
+    assert np.abs(f12 - (0.7 * f1 - 1.3 * f2)).max() <= 1e-13 * scale
+    _, fd = oracle.primal_tangent(g, E, F1, T, Fdot=F2)
+    assert np.abs(fd - f2).max() <= 1e-13 * np.abs(f2).max()
+
+
 def test_monitor_is_mean_squared_displacement():
     nx = 6
     rng = np.random.default_rng(0)
