@@ -208,6 +208,22 @@ def time_to_gradient(torch, lbm, I, reps: int = 3):
     out["plate_young_64"] = timed(s, torch.tensor([np.sqrt(0.15)], dtype=torch.float64,
                                                   device="cuda"), 1)
     s.close()
+    # clamped-left / tensioned plate (zero body force, nu = 0.3), target = its own state at
+    # E = 1; scalar modulus control evaluated at E = 1.5, and a per-node modulus field
+    # (N controls) evaluated at a lognormal field around E = 1
+    geo, wd, wT = I.baseline_plate(64)
+    N = geo.nx * geo.nx
+    for control, at in (("young_scalar", np.array([np.sqrt(1.5)])),
+                        ("young_field", np.sqrt(I.lognormal_E(N, E_ref=1.0, seed=0)))):
+        s = lbm.LBMSolid(geo.nx, geo.nx, geo.dx, 1.0, 0.3, periodic=False,
+                         node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
+                         wall_n=geo.normal, control=control)
+        s.set_control(torch.ones(at.size, dtype=torch.float64, device="cuda"))
+        s.primal_solve(4_000_000, tol=1e-12, criterion=1, check_every=64)
+        s.set_target(s.displacement())
+        out["baseline_plate_%s_64" % control] = timed(s, torch.as_tensor(at, device="cuda"),
+                                                       at.size)
+        s.close()
     return out
 
 
