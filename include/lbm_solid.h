@@ -257,7 +257,8 @@ lbm_status lbm_unet_create(int base, int levels, int batch, int H, int W,
 lbm_status lbm_unet_destroy(lbm_unet *u);
 long lbm_unet_param_count(const lbm_unet *u); /* -1 for NULL */
 /* Synchronises the stream; LBM_ERR_CUDA if a tensor-core convolution of this network
-   gave up waiting for its own matrix operations (its outputs were then set to NaN). */
+   gave up waiting for its own matrix operations since the last call (its outputs were
+   then set to NaN).  Reading the flag clears it. */
 lbm_status lbm_unet_status(lbm_unet *u);
 /* Copies the parameter vector (which = 0) or the last gradient (which = 1) into dst. */
 lbm_status lbm_unet_get_params(lbm_unet *u, float *dst_dev, int which);

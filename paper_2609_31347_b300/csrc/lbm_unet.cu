@@ -455,11 +455,8 @@ void conv3_tc(lbm_unet *u, const TIN *in, int Cin, const bf16 *w, int Cout, cons
   size_t smem = 2 * ((size_t)tc::kM * kc * 2 * (split ? 2 : 1) + (size_t)nt * kc * 2);
   // at most 512 / tcols CTAs per SM, so that their TMEM allocations always fit
   if (smem < (size_t)tcols * 456) smem = (size_t)tcols * 456;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc::k_conv3<TIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  // the opt-in shared-memory size is per device: set it on every launch (cheap)
+  cudaFuncSetAttribute(tc::k_conv3<TIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   dim3 grid((unsigned)mt, (unsigned)(Cout / nt));
   tc::k_conv3<TIN><<<grid, tc::kThreads, smem, u->stream>>>(in, Cin, w, Cout, bias, out_bf, out_f,
                                                            u->B, Hh, Ww, sgn, kc, nt, tcols, u->err);
@@ -659,6 +656,7 @@ lbm_status lbm_unet_status(lbm_unet *u) {
   if (cudaMemcpyAsync(&h, u->err, sizeof(int), cudaMemcpyDeviceToHost, u->stream) != cudaSuccess ||
       cudaStreamSynchronize(u->stream) != cudaSuccess)
     return LBM_ERR_CUDA;
+  if (h && cudaMemsetAsync(u->err, 0, sizeof(int), u->stream) != cudaSuccess) return LBM_ERR_CUDA;
   return h ? LBM_ERR_CUDA : LBM_OK;
 }
 
