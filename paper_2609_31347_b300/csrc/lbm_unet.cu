@@ -452,7 +452,7 @@ void conv3_tc(lbm_unet *u, const TIN *in, int Cin, const bf16 *w, int Cout, cons
   int tcols = 32;
   while (tcols < nt) tcols *= 2;
   const bool split = sizeof(TIN) == 4;
-  size_t smem = 2 * ((size_t)tc::kM * kc * 2 * (split ? 2 : 1) + (size_t)nt * kc * 2);
+  size_t smem = tc::kBufs * ((size_t)tc::kM * kc * 2 * (split ? 2 : 1) + (size_t)nt * kc * 2);
   // at most 512 / tcols CTAs per SM, so that their TMEM allocations always fit
   if (smem < (size_t)tcols * 456) smem = (size_t)tcols * 456;
   // the opt-in shared-memory size is per device: set it on every launch (cheap)

@@ -11,10 +11,11 @@
 // into shared memory (cp.async, 16 B per copy; FP32 activations are split into high and
 // low BF16 parts on the way, two A tiles, two MMAs), in the no-swizzle K-major layout of
 // 8-row x 16-byte core matrices; one thread issues Kc/16 tcgen05.mma (kind::f16, BF16
-// inputs, FP32 accumulation) per chunk and commits them to the buffer's mbarrier.  Two
-// buffers: the copies of chunk i + 1 are in flight while chunk i is multiplied.  The epilogue reads the
-// accumulator with tcgen05.ld (warp w: lanes 32w..32w+31), adds the bias and stores
-// BF16 or FP32 rows.
+// inputs, FP32 accumulation) per chunk and commits them to the buffer's mbarrier.  Three
+// buffers: the copies of chunk i + 1 are in flight while chunks i - 1 and i multiply, so
+// the tensor core gets chunk i without waiting for chunk i - 1 to finish.  The epilogue
+// reads the accumulator with tcgen05.ld (warp w: lanes 32w..32w+31), adds the bias and
+// stores BF16 or FP32 rows.
 //
 // Every mbarrier wait is bounded; on a timeout the CTA sets *err, stops issuing, waits
 // (bounded) for what it issued, writes NaN to its outputs, frees its TMEM and returns.
@@ -28,6 +29,7 @@ namespace tc {
 constexpr int kM = 128;        // pixels per CTA = TMEM lanes
 constexpr int kThreads = 128;  // four warps
 constexpr long kSpin = 1L << 22;
+constexpr int kBufs = 3;       // operand buffers: chunk i + 1 loads while i and i - 1 multiply
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
     int B, int H, int W, int sgn, int kc, int nt, int tcols, int *__restrict__ err) {
   constexpr bool kSplit = sizeof(TIN) == 4;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[kBufs];
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long P = (long)B * H * W;
@@ -110,8 +112,8 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
   const uint32_t sbase = smem_u32(smem);
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    for (int b2 = 0; b2 < kBufs; ++b2)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[b2])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -149,9 +151,9 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
       rb[i] = (t / H) * H;
     }
   }
-  // stage the operands of K-chunk `it` into buffer it & 1
+  // stage the operands of K-chunk `it` into buffer it % kBufs
   auto load = [&](int it) {
-    const int buf = it & 1;
+    const int buf = it % kBufs;
     const int tap = it / ksteps, k0 = (it % ksteps) * kc;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     const uint32_t abase = sbase + buf * buf_bytes;
@@ -208,10 +210,12 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
   };
   load(0);
   for (int it = 0; it < iters; ++it) {
-    // prefetch chunk it + 1 into the other buffer once the MMAs of chunk it - 1, which
-    // read it, are done (block-uniform decision)
+    // prefetch chunk it + 1 once the MMAs of chunk it + 1 - kBufs, the last to read its
+    // buffer, are done (block-uniform decision); chunk it's MMAs then never wait for
+    // chunk it - 1's
     if (it + 1 < iters) {
-      const bool w_ok = it < 1 || wait_bar(&bar[(it + 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
+      const int prev = it + 1 - kBufs;
+      const bool w_ok = prev < 0 || wait_bar(&bar[(it + 1) % kBufs], (uint32_t)((prev / kBufs) & 1));
       if (!__syncthreads_and(w_ok)) {
         ok = false;
         break;
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
-      const uint32_t abase = sbase + (it & 1) * buf_bytes;
+      const uint32_t abase = sbase + (it % kBufs) * buf_bytes;
       const uint32_t bbase = abase + a_bytes * (kSplit ? 2 : 1);
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t sbo = (uint32_t)kc * 16;
@@ -233,16 +237,16 @@ __global__ void __launch_bounds__(kThreads) k_conv3(
         mma(tmem, sdesc(abase + j * 256, 128, sbo), bd, id, (it > 0 || j > 0) ? 1u : 0u);
         if (kSplit) mma(tmem, sdesc(abase + a_bytes + j * 256, 128, sbo), bd, id, 1u);
       }
-      commit(&bar[it & 1]);
+      commit(&bar[it % kBufs]);
     }
   }
   // the last commit covers every MMA issued before it
-  if (ok) ok = wait_bar(&bar[(iters - 1) & 1], (uint32_t)(((iters - 1) >> 1) & 1));
+  if (ok) ok = wait_bar(&bar[(iters - 1) % kBufs], (uint32_t)(((iters - 1) / kBufs) & 1));
   ok = __syncthreads_and(ok);
   if (!ok) {
     atomicExch(err, 1);
     // let anything still queued drain before the accumulator is released
-    for (int b2 = 0; b2 < 2; ++b2) wait_bar(&bar[b2], 0), wait_bar(&bar[b2], 1);
+    for (int b2 = 0; b2 < kBufs; ++b2) wait_bar(&bar[b2], 0), wait_bar(&bar[b2], 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   // epilogue: warp w holds rows 32w + lane
