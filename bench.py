@@ -304,7 +304,7 @@ def plate_throughput(torch, lbm, I, Nx: int = 1024, sweeps: int = 200):
     return out
 
 
-def warm_start(torch, lbm, I, samples: int = 2048, steps: int = 2500, seed: int = 1):
+def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 2500, seed: int = 1):
     """Learned warm start (not in the paper): primal and adjoint networks trained on
     `samples` solver-generated 128^2 steady states each (random 8-mode fields), then
     iterations and wall time to residual 1e-10 cold vs warm on held-out 8-mode controls
@@ -501,7 +501,7 @@ def main():
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gradient runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
-    ap.add_argument("--warm-samples", type=int, default=2048,
+    ap.add_argument("--warm-samples", type=int, default=10000,
                     help="training states per network for the warm start")
     ap.add_argument("--kernel", default="auto", choices=["auto", "fp64"],
                     help="sweep arithmetic: integer-pipe fixed point (auto) or FP64 pipe")
