@@ -140,64 +140,117 @@ __global__ void __launch_bounds__(128) k_conv(const TIN *__restrict__ in, int Ci
   }
 }
 
-// Weight gradient: gw[tap][ci][co] += sum_p in[p + tap, ci] gout[p, co] (M = co, N = ci,
-// K = pixels).  One warp: 16 output channels x 64 input channels over a chunk of 256
-// pixels; grid = (pixel chunks / 4, co / 16, taps * ci tiles of 64).  Only the real
-// channels (ci < ci_real, co < co_real) are accumulated (FP32 atomics) into the
-// unpadded [tap][ci_real][co_real] slice.
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+// Weight gradient: gw[tap][ci][co] += sum_p in[p + tap, ci] gout[p, co], a GEMM with
+// M = co, N = ci, K = pixels.  A block owns 64 output x 64 input channels of one tap and
+// `ppb` consecutive pixels.  Per 64-pixel stage the 128 threads copy the gout rows
+// (A, [pixel][co]) and the shifted input rows (B, [pixel][ci]) into shared memory with
+// cp.async (two buffers, rows padded to 144 B so that ldmatrix is conflict-free); each
+// warp reads its 16 output channels transposed with ldmatrix.trans into
+// mma.sync.m16n8k16 fragments (K = 16 pixels per step).  The FP32 sums of the block are
+// added into the unpadded [tap][ci_real][co_real] slice with atomics; only real channels
+// are written.  Needs Cin, Cout multiples of 16.
 template <int KS>
 __global__ void __launch_bounds__(128) k_conv_wgrad(const bf16 *__restrict__ in, int Cin,
                                                     int ci_real, const bf16 *__restrict__ gout,
                                                     int Cout, int co_real,
-                                                    float *__restrict__ gw, int B, int H, int W) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                                                    float *__restrict__ gw, int B, int H, int W,
+                                                    long ppb) {
+  constexpr int kP = 64, kLd = 72;
+  __shared__ __align__(16) bf16 sA[2][kP * kLd];
+  __shared__ __align__(16) bf16 sB[2][kP * kLd];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
   const int nci = (Cin + 63) / 64;
   const int tap = blockIdx.z / nci, cit = blockIdx.z % nci;
   const int R = KS / 2, dy = tap / KS - R, dx = tap % KS - R;
-  const int m0 = blockIdx.y * 16;  // co tile
-  const int c0 = cit * 64;          // ci tile
-  const int nt = (Cin - c0) / 8 < 8 ? (Cin - c0) / 8 : 8;
+  const int co0 = blockIdx.y * 64, ci0 = cit * 64;
+  const int mt = Cout - co0 < 64 ? Cout - co0 : 64;  // multiples of 16
+  const int ntl = Cin - ci0 < 64 ? Cin - ci0 : 64;
   const long P = (long)B * H * W;
-  const long chunk = 256;
-  const long pstart = ((long)blockIdx.x * 4 + warp) * chunk;
-  if (pstart >= P) return;
+  const long pb = (long)blockIdx.x * ppb;
+  if (pb >= P) return;
+  const long pe = pb + ppb < P ? pb + ppb : P;
+  const int stages = (int)((pe - pb + kP - 1) / kP);
+  auto load = [&](int st, int buf) {
+    const long ps = pb + (long)st * kP;
+    const int ca = mt / 8, cb = ntl / 8;
+    for (int q = tid; q < kP * ca; q += 128) {
+      const int r = q / ca, c = q - r * ca;
+      const long p = ps + r;
+      const bool v = p < pe;
+      tc::cp16(tc::smem_u32(&sA[buf][r * kLd + c * 8]), gout + (v ? p : 0) * Cout + co0 + c * 8, v);
+    }
+    for (int q = tid; q < kP * cb; q += 128) {
+      const int r = q / cb, c = q - r * cb;
+      const long p = ps + r;
+      const bool v = p < pe;
+      long row = 0;
+      if (v) {
+        const int x = (int)(p % W);
+        const long rr = p / W;
+        const int y = (int)(rr % H);
+        const long b = rr / H;
+        int ys = y + dy, xs = x + dx;
+        ys = ys < 0 ? ys + H : (ys >= H ? ys - H : ys);
+        xs = xs < 0 ? xs + W : (xs >= W ? xs - W : xs);
+        row = (b * H + ys) * W + xs;
+      }
+      tc::cp16(tc::smem_u32(&sB[buf][r * kLd + c * 8]), in + row * Cin + ci0 + c * 8, v);
+    }
+    asm volatile("cp.async.commit_group;");
+  };
   float acc[8][4];
 #pragma unroll
   for (int j = 0; j < 8; ++j)
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
-  auto src = [&](long p) -> long {
-    const int x = (int)(p % W);
-    const long r = p / W;
-    const int y = (int)(r % H), b = (int)(r / H);
-    const int ys = ((y + dy) % H + H) % H, xs = ((x + dx) % W + W) % W;
-    return (((long)b * H + ys) * W + xs) * Cin;
-  };
-  for (long k0 = pstart; k0 < pstart + chunk && k0 < P; k0 += 16) {
-    uint32_t a[4];
-    const long p0 = k0 + 2 * t, p1 = p0 + 1, p8 = p0 + 8, p9 = p0 + 9;
-    a[0] = pack2(gout[p0 * Cout + m0 + g], gout[p1 * Cout + m0 + g]);
-    a[1] = pack2(gout[p0 * Cout + m0 + g + 8], gout[p1 * Cout + m0 + g + 8]);
-    a[2] = pack2(gout[p8 * Cout + m0 + g], gout[p9 * Cout + m0 + g]);
-    a[3] = pack2(gout[p8 * Cout + m0 + g + 8], gout[p9 * Cout + m0 + g + 8]);
-    const long s0 = src(p0), s1 = src(p1), s8 = src(p8), s9 = src(p9);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (j >= nt) break;
-      const int ci = c0 + 8 * j + g;
-      uint32_t bb[2];
-      bb[0] = pack2(in[s0 + ci], in[s1 + ci]);
-      bb[1] = pack2(in[s8 + ci], in[s9 + ci]);
-      mma16816(acc[j], a, bb);
+  const bool active = 16 * warp < mt;
+  const int tile = lane >> 3, rr8 = lane & 7;
+  load(0, 0);
+  for (int st = 0; st < stages; ++st) {
+    if (st + 1 < stages) {
+      load(st + 1, (st + 1) & 1);
+      asm volatile("cp.async.wait_group 1;");
+    } else {
+      asm volatile("cp.async.wait_group 0;");
     }
+    __syncthreads();
+    const bf16 *A = sA[st & 1], *Bm = sB[st & 1];
+    if (active) {
+#pragma unroll
+      for (int k0 = 0; k0 < kP; k0 += 16) {
+        // A fragment: tiles (m 0-7, k 0-7), (m 8-15, k 0-7), (m 0-7, k 8-15), (m 8-15, k 8-15)
+        uint32_t a[4];
+        ldsm_x4_trans(a, tc::smem_u32(&A[(k0 + rr8 + ((tile & 2) ? 8 : 0)) * kLd + 16 * warp +
+                                          ((tile & 1) ? 8 : 0)]));
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          if (8 * j >= ntl) break;
+          // B fragments of n-tiles j, j + 1: (k 0-7, n), (k 8-15, n), (k 0-7, n+8), (k 8-15, n+8)
+          uint32_t b4[4];
+          ldsm_x4_trans(b4, tc::smem_u32(&Bm[(k0 + rr8 + ((tile & 1) ? 8 : 0)) * kLd + 8 * j +
+                                             ((tile & 2) ? 8 : 0)]));
+          const uint32_t b0[2] = {b4[0], b4[1]}, b1[2] = {b4[2], b4[3]};
+          mma16816(acc[j], a, b0);
+          mma16816(acc[j + 1], a, b1);
+        }
+      }
+    }
+    __syncthreads();  // this buffer is refilled two stages on
   }
+  if (!active) return;
   float *dst = gw + (long)tap * ci_real * co_real;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    if (j >= nt) break;
-    const int ci = c0 + 8 * j + 2 * t;
-    const int ma = m0 + g, mb = m0 + g + 8;
+    if (8 * j >= ntl) break;
+    const int ci = ci0 + 8 * j + 2 * t;
+    const int ma = co0 + 16 * warp + g, mb = ma + 8;
     if (ci < ci_real && ma < co_real) atomicAdd(dst + (long)ci * co_real + ma, acc[j][0]);
     if (ci + 1 < ci_real && ma < co_real) atomicAdd(dst + (long)(ci + 1) * co_real + ma, acc[j][1]);
     if (ci < ci_real && mb < co_real) atomicAdd(dst + (long)ci * co_real + mb, acc[j][2]);
@@ -538,13 +591,14 @@ void conv_bwd(lbm_unet *u, Layer &l, const bf16 *gout, int Hh, int Ww, bool need
     else
       k_conv<1, bf16><<<grid, 128, 0, u->stream>>>(gout, l.copad, l.wb, l.cipad, nullptr, l.gin, nullptr, u->B, Hh, Ww, -1);
   }
-  const long chunks = (P + 255) / 256;
+  const long ppb = 1024;  // pixels per block (K range); partial sums meet in atomics
   const unsigned nci = (unsigned)((l.cipad + 63) / 64);
-  dim3 grid((unsigned)((chunks + 3) / 4), (unsigned)(l.copad / 16), (unsigned)(l.ks * l.ks) * nci);
+  dim3 grid((unsigned)((P + ppb - 1) / ppb), (unsigned)((l.copad + 63) / 64),
+            (unsigned)(l.ks * l.ks) * nci);
   if (l.ks == 3)
-    k_conv_wgrad<3><<<grid, 128, 0, u->stream>>>(l.in, l.cipad, l.ci, gout, l.copad, l.co, u->g + l.woff, u->B, Hh, Ww);
+    k_conv_wgrad<3><<<grid, 128, 0, u->stream>>>(l.in, l.cipad, l.ci, gout, l.copad, l.co, u->g + l.woff, u->B, Hh, Ww, ppb);
   else
-    k_conv_wgrad<1><<<grid, 128, 0, u->stream>>>(l.in, l.cipad, l.ci, gout, l.copad, l.co, u->g + l.woff, u->B, Hh, Ww);
+    k_conv_wgrad<1><<<grid, 128, 0, u->stream>>>(l.in, l.cipad, l.ci, gout, l.copad, l.co, u->g + l.woff, u->B, Hh, Ww, ppb);
   k_bias_grad<<<148 * 4, l.co, 0, u->stream>>>(gout, l.co, l.copad, P, u->g + l.boff);
 }
 
