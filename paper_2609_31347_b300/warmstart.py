@@ -173,6 +173,11 @@ class WarmStartNet:
         if nxf % self.nx:
             raise ValueError("lattice size %d is not a multiple of the network's %d" % (nxf, self.nx))
         factor = nxf // self.nx
+        N = nxf * nxf
+        L._dev_ptr(field, 2 * N)  # CUDA float64, contiguous, right size (raises otherwise)
+        L._dev_ptr(out, 8 * N)
+        if ref is not None:
+            L._dev_ptr(ref, 2 * N)
         dxf = 1.0 / nxf if dx_fine is None else float(dx_fine)
         net = self._inference_net()
         self._check(self._lib.lbm_warm_encode(1, nxf, nxf, factor, _ptr(field), _ptr(ref),
