@@ -304,7 +304,7 @@ def plate_throughput(torch, lbm, I, Nx: int = 1024, sweeps: int = 200):
     return out
 
 
-def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 2500, seed: int = 1):
+def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 8000, seed: int = 1):
     """Learned warm start (not in the paper): primal and adjoint networks trained on
     `samples` solver-generated 128^2 steady states each (random 8-mode fields), then
     iterations and wall time to residual 1e-10 cold vs warm on held-out 8-mode controls
