@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -36,6 +37,7 @@ BYTES_PER_LUP = 144  # 64 B populations in + 64 B out + 16 B force (primal) or r
 FP64_OPS_PER_LUP = 37
 FP64_LANES_PER_SM = 2  # B300: measured 1.86 DFMA/clk/SM in a throughput probe
 NUM_SMS = 148
+HBM_NOMINAL_GBS = 7700.0  # B300 HBM3e nominal bandwidth (context beside the measured peak)
 
 
 def peaks():
@@ -431,6 +433,87 @@ def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 8000, seed: int
     return out
 
 
+def plate_identification(torch, lbm, I):
+    """Young's-modulus identification on the clamped / tensioned plate (target: its own
+    state at E = 1): scalar E from E = 0.5 at N_x = 64, and a per-node modulus field from
+    a uniform E = 0.5 towards a lognormal field (sigma 0.2) at N_x = 32.  L-BFGS runs cold
+    (every solve from rest, as in the paper) and records its evaluation points; the same
+    points are then evaluated with every solve started from the history of steady states
+    (primal: last state, or for the scalar modulus the extrapolation in 1/E of the last
+    three; adjoint: the previous adjoint states combined to fit the new source), so both
+    runs reach the same control error and only the solver time differs.  The
+    learned networks do not apply here: they map periodic force fields, while the plate
+    is driven by its wall traction and controlled through the modulus."""
+    from paper_2609_31347_b300 import gbo
+    from paper_2609_31347_b300 import warmstart as W
+    out = {}
+    for name, Nx, control, m_max in (("young_scalar_64", 64, "young_scalar", 10),
+                                     ("young_field_32", 32, "young_field", 6)):
+        geo, wd, wT = I.baseline_plate(Nx)
+        N = geo.nx * geo.nx
+        Estar = np.ones(1) if control == "young_scalar" else I.lognormal_E(N, E_ref=1.0, seed=3)
+
+        def solver():
+            s = lbm.LBMSolid(geo.nx, geo.nx, geo.dx, 1.0, 0.3, periodic=False,
+                             node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
+                             wall_n=geo.normal, control=control)
+            s.set_control(torch.as_tensor(np.sqrt(Estar), device="cuda"))
+            s.primal_solve(4_000_000, tol=1e-12, criterion=1, check_every=64)
+            s.set_target(s.displacement())
+            s.sweeps["primal_solve"] = 0
+            return s
+
+        opts = gbo.SolveOpts(tol=1e-10, max_steps=4_000_000)
+        a0 = torch.full((Estar.size,), np.sqrt(0.5), dtype=torch.float64, device="cuda")
+        pts, ref = [], []
+        s = solver()
+        fg = gbo.make_fg(s, opts, opts)
+        # L-BFGS stops once the gradient fell by 1e-5; beyond that the objective reaches
+        # the level of the solves' own residual error
+        eps = 1e-5 * float(torch.linalg.vector_norm(fg(a0)[1]))
+        s.sweeps.clear()
+
+        def rec(a):
+            pts.append(a.detach().clone())
+            ref.append(fg(a))
+            return ref[-1]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = gbo.lbfgs(rec, a0, m_max=m_max, eps=eps)
+        torch.cuda.synchronize()
+        t_cold = time.perf_counter() - t0
+        act = torch.as_tensor(geo.active.astype(bool), device="cuda")
+        E_got = (r.alpha ** 2)[act] if control == "young_field" else r.alpha ** 2
+        E_ref = torch.as_tensor(Estar, device="cuda")[act] if control == "young_field" \
+            else torch.as_tensor(Estar, device="cuda")
+        res = {"controls": int(Estar.size), "lbfgs_steps": r.steps, "stop": r.reason,
+               "evaluations": len(pts),
+               "J0": r.history[0]["J"], "J": r.J,
+               "modulus_rel_err": float((E_got - E_ref).abs().max() / E_ref.abs().max()),
+               "cold": {"s": t_cold, "sweeps": s.sweeps.get("primal_solve", 0) + s.sweeps.get("adjoint_solve", 0)}}
+        s.close()
+        s = solver()
+        fgw = gbo.make_fg(s, opts, opts, warm=W.WarmStarter(history=3))
+        # differences relative to the first point's J and gradient (J -> 0 at the optimum)
+        J0, g0 = ref[0][0], float(ref[0][1].abs().max())
+        dJ = dg = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, (J, g) in zip(pts, ref):
+            Jw, gw = fgw(a)
+            if math.isfinite(J):
+                dJ = max(dJ, abs(Jw - J) / J0)
+                dg = max(dg, float((gw - g).abs().max()) / g0)
+        torch.cuda.synchronize()
+        res["warm"] = {"s": time.perf_counter() - t0,
+                       "sweeps": s.sweeps.get("primal_solve", 0) + s.sweeps.get("adjoint_solve", 0),
+                       "max_diff_J_rel_J0": dJ, "max_diff_grad_rel_g0": dg}
+        s.close()
+        res["speedup"] = res["cold"]["s"] / res["warm"]["s"]
+        out[name] = res
+    return out
+
+
 def cpu_baseline(seconds_target: float = 12.0):
     """The oracle as it stands, single thread, on a bounded sample: 512^2, primal then
     adjoint sweeps of the same workload kind."""
@@ -609,7 +692,8 @@ def main():
                 "frac": achieved_gbs / hbm_gbs, "traffic": traffic, "kernel": kname,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_lup": BYTES_PER_LUP,
-                "units_per_launch": N}
+                "units_per_launch": N,
+                "nominal": {"peak": HBM_NOMINAL_GBS, "frac": achieved_gbs / HBM_NOMINAL_GBS}}
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -651,6 +735,7 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_ttg:
         extra("time_to_gradient", lambda: time_to_gradient(torch, lbm, I))
+        extra("plate_identification", lambda: plate_identification(torch, lbm, I))
     if rank == 0 and world == 1 and not args.no_batch:
         s.close()
         extra("batch_256", lambda: batch_throughput(torch, lbm, I))

@@ -172,9 +172,10 @@ lbm_status lbm_solid_tangent(lbm_solid *h, const double *seed_dev, size_t n,
                              lbm_solve_info *info);
 
 /* Populations: which = 0 primal f_S, 1 adjoint phi_S, 2 adjoint phi_C; 8N device
-   doubles.  set_populations(0) sets f_S (warm start / checkpoint restore);
-   set_populations(2) sets phi_C (adjoint warm start, used by the next adjoint solve
-   when opts.fixed_steps is set and keep is requested via adjoint warm start). */
+   doubles.  set_populations(0) sets f_S (warm start / checkpoint restore; the next
+   primal solve continues from it).  set_populations(2) sets phi_C as the initial state
+   of the next adjoint solve only; every other adjoint solve starts from rest (and
+   set_control / primal_solve discard a pending one). */
 lbm_status lbm_solid_get_populations(lbm_solid *h, int which, double *dst_dev);
 lbm_status lbm_solid_set_populations(lbm_solid *h, int which, const double *src_dev);
 
@@ -321,6 +322,32 @@ lbm_status lbm_warm_decode(int count, int wc, int hc, int factor, double dx_fine
                            double *pop_dev, int accumulate, void *stream);
 /* rms_i of channel i of an (pixels, 8) tensor over its first min(pixels, 2^22) rows. */
 lbm_status lbm_warm_channel_rms(const float *t_dev, long pixels, float *rms_dev, void *stream);
+
+/* ---- Initial states from the history of an optimisation loop ----------------------
+ * The paper has no counterpart (every solve there starts from rest).  An optimisation
+ * loop keeps its last few steady states; the next solve starts from a combination of
+ * them, e.g. the Lagrange extrapolation of the primal state in 1/E for a Young's-modulus
+ * control (the steady displacement scales with 1/E for loads that do not depend on E),
+ * or, for the adjoint, the combination of previous adjoint states whose sources best
+ * fit the new source in least squares (the adjoint steady state is linear in its
+ * source).  The solver then iterates to the same tolerance, so only iteration counts
+ * change.  These two calls do the vector arithmetic.
+ *
+ * dst[i] = sum_{j < count} w[j] * src_dev[j][i] for i < n.  1 <= count <= 4; w and
+ * src_dev are host arrays of count weights and count device pointers to n doubles; dst
+ * (device, n doubles) may be one of the sources.  Stream-ordered, no synchronisation.
+ * Errors: LBM_ERR_ARG (count out of range, n < 1, a NULL pointer), LBM_ERR_CUDA. */
+lbm_status lbm_warm_combine(int count, long n, const double *w, const double *const *src_dev,
+                            double *dst_dev, void *stream);
+/* Doubles of device scratch that lbm_warm_dots needs. */
+long lbm_warm_dot_work_size(void);
+/* Inner products of m device vectors of n doubles (1 <= m <= 5): out_host[a*m + b] =
+ * sum_i v_dev[a][i] * v_dev[b][i], summed in a fixed order (repeatable bit for bit).
+ * work_dev: caller-owned device scratch of lbm_warm_dot_work_size() doubles, not used
+ * by another call at the same time.  Synchronises the stream (the result is on the
+ * host).  Errors: LBM_ERR_ARG (m out of range, n < 1, a NULL pointer), LBM_ERR_CUDA. */
+lbm_status lbm_warm_dots(int m, long n, const double *const *v_dev, double *work_dev,
+                         double *out_host, void *stream);
 
 /* Objective without any device allocation.
  *

@@ -321,6 +321,76 @@ __global__ void __launch_bounds__(1024) k_channel_rms(const float *__restrict__ 
   if (threadIdx.x == 0) rms[ch] = (float)sqrt(sm[0] / (double)n);
 }
 
+// ---- History of steady states: combinations and inner products --------------------
+
+constexpr int kMaxVec = 4;                       // history vectors per call
+constexpr int kDotBlocks = 296;                  // 2 blocks per SM, grid-stride
+constexpr int kDotPairs = (kMaxVec + 1) * (kMaxVec + 2) / 2;
+
+struct VecSet {
+  const double *v[kMaxVec + 1];
+  double w[kMaxVec];
+};
+
+// dst[i] = sum_j w_j src_j[i].  Each element reads every source before it is written, so
+// dst may be one of the sources.
+__global__ void __launch_bounds__(256) k_combine(VecSet vs, int count, long n,
+                                                 double *__restrict__ dst) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < count; ++j) acc += vs.w[j] * vs.v[j][i];
+    dst[i] = acc;
+  }
+}
+
+// Per-block partial sums of u_a . u_b for a <= b < m, in the packed upper-triangle order
+// p(a, b) = a * m - a (a - 1) / 2 + (b - a); grid-stride over n, fixed order.
+__global__ void __launch_bounds__(256) k_dot_partial(VecSet vs, int m, long n,
+                                                     double *__restrict__ part) {
+  double acc[kDotPairs];
+#pragma unroll
+  for (int p = 0; p < kDotPairs; ++p) acc[p] = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    double u[kMaxVec + 1];
+#pragma unroll
+    for (int a = 0; a <= kMaxVec; ++a) u[a] = a < m ? vs.v[a][i] : 0.0;
+    int p = 0;
+#pragma unroll
+    for (int a = 0; a <= kMaxVec; ++a)
+#pragma unroll
+      for (int b = a; b <= kMaxVec; ++b) acc[p++] += u[a] * u[b];
+  }
+  __shared__ double sm[kDotPairs][256];
+#pragma unroll
+  for (int p = 0; p < kDotPairs; ++p) sm[p][threadIdx.x] = acc[p];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int p = 0; p < kDotPairs; ++p) sm[p][threadIdx.x] += sm[p][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < kDotPairs) part[threadIdx.x * kDotBlocks + blockIdx.x] = sm[threadIdx.x][0];
+}
+
+// Sums the partials of each pair in block order and expands the packed triangle (full
+// (kMaxVec + 1)^2 layout, only the first m x m used) into out.
+__global__ void k_dot_finish(const double *__restrict__ part, int m, double *__restrict__ out) {
+  const int t = threadIdx.x;
+  if (t >= kDotPairs) return;
+  double acc = 0.0;
+  for (int b = 0; b < kDotBlocks; ++b) acc += part[t * kDotBlocks + b];
+  int p = 0;
+  for (int a = 0; a <= kMaxVec; ++a)
+    for (int b = a; b <= kMaxVec; ++b, ++p)
+      if (p == t && b < m) {
+        out[a * m + b] = acc;
+        out[b * m + a] = acc;
+      }
+}
+
 unsigned grid_for(long n) {
   const long b = (n + 255) / 256;
   return (unsigned)(b < 148 * 16 ? (b < 1 ? 1 : b) : 148 * 16);
@@ -377,6 +447,41 @@ lbm_status lbm_warm_channel_rms(const float *t_dev, long pixels, float *rms_dev,
   if (!t_dev || pixels < 1 || !rms_dev) return LBM_ERR_ARG;
   k_channel_rms<<<8, 1024, 0, (cudaStream_t)stream>>>(t_dev, pixels, rms_dev);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+lbm_status lbm_warm_combine(int count, long n, const double *w, const double *const *src_dev,
+                            double *dst_dev, void *stream) {
+  if (count < 1 || count > kMaxVec || n < 1 || !w || !src_dev || !dst_dev) return LBM_ERR_ARG;
+  VecSet vs{};
+  for (int j = 0; j < count; ++j) {
+    if (!src_dev[j]) return LBM_ERR_ARG;
+    vs.v[j] = src_dev[j];
+    vs.w[j] = w[j];
+  }
+  k_combine<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(vs, count, n, dst_dev);
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+long lbm_warm_dot_work_size(void) { return (long)kDotPairs * kDotBlocks + kDotPairs * 2 + 64; }
+
+lbm_status lbm_warm_dots(int m, long n, const double *const *v_dev, double *work_dev,
+                         double *out_host, void *stream) {
+  if (m < 1 || m > kMaxVec + 1 || n < 1 || !v_dev || !work_dev || !out_host) return LBM_ERR_ARG;
+  VecSet vs{};
+  for (int j = 0; j < m; ++j) {
+    if (!v_dev[j]) return LBM_ERR_ARG;
+    vs.v[j] = v_dev[j];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double *part = work_dev, *res = work_dev + (long)kDotPairs * kDotBlocks;
+  k_dot_partial<<<kDotBlocks, 256, 0, st>>>(vs, m, n, part);
+  k_dot_finish<<<1, 32, 0, st>>>(part, m, res);
+  if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+  if (cudaMemcpyAsync(out_host, res, sizeof(double) * m * m, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  return LBM_OK;
 }
 
 }  // extern "C"

@@ -36,6 +36,7 @@ EXPORTED = [
     "lbm_unet_create", "lbm_unet_destroy", "lbm_unet_param_count", "lbm_unet_get_params",
     "lbm_unet_set_params", "lbm_unet_forward", "lbm_unet_train_step", "lbm_unet_status",
     "lbm_solid_adjoint_source", "lbm_warm_encode", "lbm_warm_targets", "lbm_warm_decode", "lbm_warm_channel_rms",
+    "lbm_warm_combine", "lbm_warm_dot_work_size", "lbm_warm_dots",
 ]
 
 
@@ -121,6 +122,9 @@ def load_library(path: str = LIB_PATH):
         "lbm_warm_targets": ([I, I, I, D, I, P, P, P, P, P], I),
         "lbm_warm_decode": ([I, I, I, I, D, I, P, P, P, P, I, P], I),
         "lbm_warm_channel_rms": ([P, ctypes.c_long, P, P], I),
+        "lbm_warm_combine": ([I, ctypes.c_long, P, P, P, P], I),
+        "lbm_warm_dot_work_size": ([], ctypes.c_long),
+        "lbm_warm_dots": ([I, ctypes.c_long, P, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -157,6 +161,49 @@ def _dev_ptr(t, n=None, dtype=None):
     if n is not None and t.numel() != n:
         raise ValueError("expected %d values, got %d" % (n, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptr_array(tensors, n):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for j, t in enumerate(tensors):
+        arr[j] = _dev_ptr(t, n).value
+    return arr
+
+
+def warm_combine(weights, srcs, dst):
+    """dst = sum_j weights[j] * srcs[j] (1 to 4 device FP64 vectors of dst's size) on the
+    current stream; dst may be one of srcs."""
+    import torch
+    lib = load_library()
+    n = dst.numel()
+    w = _host(weights, np.float64, len(srcs))
+    st = lib.lbm_warm_combine(len(srcs), n, w.ctypes.data, _ptr_array(srcs, n),
+                              _dev_ptr(dst, n), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_warm_combine: " + lib.lbm_status_string(st).decode())
+    return dst
+
+
+_dot_work = {}
+
+
+def warm_dots(vectors):
+    """Matrix of inner products of 1 to 5 device FP64 vectors of one size (host, m x m),
+    summed in a fixed order; synchronises the current stream."""
+    import torch
+    lib = load_library()
+    dev = vectors[0].device
+    work = _dot_work.get(dev)
+    if work is None:
+        work = torch.empty(int(lib.lbm_warm_dot_work_size()), dtype=torch.float64, device=dev)
+        _dot_work[dev] = work
+    n, m = vectors[0].numel(), len(vectors)
+    out = np.zeros(m * m)
+    st = lib.lbm_warm_dots(m, n, _ptr_array(vectors, n), _dev_ptr(work), out.ctypes.data,
+                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_warm_dots: " + lib.lbm_status_string(st).decode())
+    return out.reshape(m, m)
 
 
 class LBMSolid:

@@ -190,65 +190,201 @@ class WarmStartNet:
         return out
 
 
-class WarmStarter:
-    """Initial states for the solves of an optimisation loop over a FORCE_FIELD control.
+def lagrange_weights(xs, x):
+    """w with sum_j w_j p(xs_j) = p(x) for every polynomial p of degree < len(xs)
+    (Lagrange interpolation/extrapolation at x from distinct abscissae xs)."""
+    xs = [float(v) for v in xs]
+    w = []
+    for i, xi in enumerate(xs):
+        t = 1.0
+        for j, xj in enumerate(xs):
+            if j != i:
+                t *= (x - xj) / (xi - xj)
+        w.append(t)
+    return np.array(w)
 
-    primal / adjoint: trained ``WarmStartNet`` or None.  reuse: start from the previous
-    steady state.  For the primal with both, the network's state of the control change
-    is added to the previous state.  For the adjoint with reuse, the previous state is
-    used alone unless ``adjoint_change`` is set: measured over an L-BFGS run on the 512^2
-    lattice, adding the network's state of the change of r cost more adjoint sweeps than
-    reusing the previous state alone, while on a single solve without a previous state
-    the adjoint network saved 20-30 % of the sweeps.  With neither a network nor reuse
-    every solve starts from rest, as in the paper."""
+
+def affine_fit_weights(G):
+    """Weights of the affine combination of vectors a_0..a_{k-1} closest to a new vector a
+    (sum_j w_j = 1, min |sum_j w_j a_j - a|), from the (k+1) x (k+1) inner products of
+    (a_0, ..., a_{k-1}, a); minimum-norm solution when the a_j are affinely dependent."""
+    k = G.shape[0] - 1
+    if k == 1:
+        return np.ones(1)
+    # a_j - a_last for j < k - 1 and a - a_last, in terms of G
+    L = k - 1
+    D = np.empty((L, L))
+    y = np.empty(L)
+    for i in range(L):
+        for j in range(L):
+            D[i, j] = G[i, j] - G[i, L] - G[L, j] + G[L, L]
+        y[i] = G[i, k] - G[i, L] - G[L, k] + G[L, L]
+    v = np.linalg.lstsq(D, y, rcond=1e-12)[0]
+    return np.concatenate([v, [1.0 - v.sum()]])
+
+
+def source_fit_weights(G):
+    """Least-squares weights of r_0..r_{k-1} for a new r (min |sum_j w_j r_j - r|), from
+    the (k+1) x (k+1) inner products of (r_0, ..., r_{k-1}, r)."""
+    k = G.shape[0] - 1
+    if not np.any(G[:k, :k]):
+        return np.zeros(k)
+    return np.linalg.lstsq(G[:k, :k], G[:k, k], rcond=1e-12)[0]
+
+
+def fit_residual(G, w):
+    """|sum_j w_j r_j - r| / |r| from the inner products G of (r_0, ..., r_{k-1}, r)."""
+    k = G.shape[0] - 1
+    c = G[k, k]
+    if c <= 0.0:
+        return 0.0
+    res2 = c - 2.0 * float(w @ G[:k, k]) + float(w @ G[:k, :k] @ w)
+    return math.sqrt(max(res2, 0.0) / c)
+
+
+class WarmStarter:
+    """Initial states for the solves of an optimisation loop.
+
+    The solver still iterates every solve to its tolerance; a start only changes the
+    number of sweeps.  Sources of a start, in the order they are tried:
+
+    - ``reuse`` with ``history`` >= 2: a combination of the last ``history`` steady
+      states.  Primal: the steady state is affine in a force control, so for force
+      controls the weights are those of the affine combination of the previous controls
+      closest to the new one (exact when the new control lies in their affine span, as
+      along a line search); for a scalar Young's modulus E = alpha^2 they extrapolate
+      (Lagrange, up to degree history - 1) in 1/E, since the steady displacement scales
+      with 1/E for loads that do not depend on E; other controls reuse the last state.
+      Adjoint: the steady state is linear in the source r, so the previous adjoint states
+      are combined with the least-squares weights that fit the new r by the previous
+      ones; if that fit leaves more than ``max_residual`` of |r| unexplained (near an
+      optimum r is mostly the primal solve's own residual error, unrelated to the earlier
+      sources), the adjoint starts from rest.  A fit whose weights exceed
+      ``max_weight`` in magnitude drops its oldest entries.
+    - ``reuse`` with ``history`` = 1: the previous steady state.
+    - primal / adjoint: trained ``WarmStartNet`` (periodic force-field controls only).
+      Without a previous state the network predicts the state; with one, the primal
+      network predicts the state of the control's change from the combined (or
+      previous) control and it is added; the adjoint network is used only when there is
+      no previous state, unless ``adjoint_change`` is set (then previous state + the
+      network's state of the change of r; measured over an L-BFGS run on the 512^2
+      lattice, that cost more adjoint sweeps than the previous state alone).
+    With neither a network nor reuse every solve starts from rest, as in the paper."""
 
     def __init__(self, primal: Optional[WarmStartNet] = None,
                  adjoint: Optional[WarmStartNet] = None, reuse: bool = True,
-                 adjoint_change: bool = False):
+                 adjoint_change: bool = False, history: int = 3, max_weight: float = 20.0,
+                 max_residual: float = 0.5):
+        if not 1 <= history <= 4:
+            raise ValueError("history must be 1..4")
         self.primal, self.adjoint, self.reuse = primal, adjoint, reuse
         self.adjoint_change = adjoint_change
-        self.F_prev = self.f_prev = self.r_prev = self.p_prev = None
+        self.history, self.max_weight = int(history), float(max_weight)
+        self.max_residual = float(max_residual)
+        self.hist_f = []  # (control, feature, steady f_S), newest last
+        self.hist_p = []  # (source r, steady adjoint state), newest last
         self._r = None
+        self._buf = None
+
+    @property
+    def f_prev(self):
+        return self.hist_f[-1][2] if self.hist_f else None
+
+    @property
+    def p_prev(self):
+        return self.hist_p[-1][1] if self.hist_p else None
+
+    def _check(self, solver):
+        if (self.primal is not None or self.adjoint is not None) and not (
+                solver.periodic and solver.control == "force_field"):
+            raise ValueError("warm-start networks serve periodic force-field controls only")
+
+    def _primal_weights(self, solver, F):
+        """(entries, weights) of the primal combination, or the newest entry alone."""
+        entries = self.hist_f[-self.history:]
+        kind = solver.control
+        while len(entries) > 1:
+            if kind == "young_scalar":
+                x = 1.0 / float(F[0]) ** 2
+                xs = [e[1] for e in entries]
+                if len(set(xs)) < len(xs) or not math.isfinite(x):
+                    entries = entries[1:]
+                    continue
+                w = lagrange_weights(xs, x)
+            elif kind in ("force_field", "force_basis2"):
+                G = L.warm_dots([e[0] for e in entries] + [F.reshape(-1)])
+                w = affine_fit_weights(G)
+            else:
+                break
+            if np.all(np.isfinite(w)) and np.abs(w).max() <= self.max_weight:
+                return entries, w
+            entries = entries[1:]
+        return entries[-1:], np.ones(1)
 
     def before_primal(self, solver, F):
-        if self.primal is None and not (self.reuse and self.f_prev is not None):
+        self._check(solver)
+        import torch
+        have_prev = self.reuse and bool(self.hist_f)
+        if self.primal is None and not have_prev:
             return
-        if self.reuse and self.f_prev is not None:
-            f0 = self.f_prev.clone()
+        N8 = 8 * solver.N
+        f0 = torch.empty(N8, dtype=torch.float64, device="cuda")
+        if have_prev:
+            entries, w = self._primal_weights(solver, F)
+            L.warm_combine(w, [e[2] for e in entries], f0)
             if self.primal is not None:
-                self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx, ref=self.F_prev,
+                ref = torch.empty_like(F.reshape(-1))
+                L.warm_combine(w, [e[0] for e in entries], ref)
+                self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx, ref=ref,
                                     accumulate=True)
         else:
-            import torch
-            f0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
             self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx)
         solver.set_populations(0, f0)
 
     def after_primal(self, solver, F):
         if self.reuse:
-            self.F_prev = F.detach().clone()
-            self.f_prev = solver.get_populations(0).clone()
+            a = F.detach().reshape(-1).clone()
+            feat = 1.0 / float(a[0]) ** 2 if solver.control == "young_scalar" else None
+            self.hist_f.append((a, feat, solver.get_populations(0).clone()))
+            del self.hist_f[:-self.history]
 
     def before_adjoint(self, solver):
-        have_prev = self.reuse and self.p_prev is not None
+        import torch
+        have_prev = self.reuse and bool(self.hist_p)
         if self.adjoint is None and not have_prev:
             return
+        self._r = solver.adjoint_source()
         if have_prev:
-            p0 = self.p_prev.clone()
+            entries = self.hist_p[-self.history:]
             if self.adjoint is not None and self.adjoint_change:
-                self._r = solver.adjoint_source()
+                p0 = entries[-1][1].clone()
                 self.adjoint.predict(self._r, p0, nx_fine=solver.nx, dx_fine=solver.dx,
-                                     ref=self.r_prev, accumulate=True)
+                                     ref=entries[-1][0], accumulate=True)
+            else:
+                p0 = torch.empty_like(entries[-1][1])
+                if len(entries) == 1 and self.history == 1:
+                    w = np.ones(1)
+                else:
+                    while True:
+                        G = L.warm_dots([e[0] for e in entries] + [self._r])
+                        w = source_fit_weights(G)
+                        if len(entries) == 1 or (np.all(np.isfinite(w)) and
+                                                 np.abs(w).max() <= self.max_weight):
+                            break
+                        entries = entries[1:]
+                    if not np.all(np.isfinite(w)) or fit_residual(G, w) > self.max_residual:
+                        if self.adjoint is None:
+                            return  # from rest
+                        w = np.zeros(len(entries))
+                L.warm_combine(w, [e[1] for e in entries], p0)
         else:
-            import torch
-            self._r = solver.adjoint_source()
             p0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
             self.adjoint.predict(self._r, p0, nx_fine=solver.nx, dx_fine=solver.dx)
         solver.set_populations(2, p0)
 
     def after_adjoint(self, solver):
         if self.reuse:
-            if self.adjoint is not None and self.adjoint_change:
-                self.r_prev = self._r if self._r is not None else solver.adjoint_source()
-            self.p_prev = solver.get_populations(2).clone()
+            r = self._r if self._r is not None else solver.adjoint_source()
+            self.hist_p.append((r, solver.get_populations(2).clone()))
+            del self.hist_p[:-self.history]
         self._r = None
