@@ -148,6 +148,30 @@ def traffic_from_profiles(kernel: str):
     return None
 
 
+def replay(torch, gbo, make_solver, pts, ref, opts, project=False, warm=None):
+    """Evaluates recorded L-BFGS points on a fresh solver (cold, or warm-started): wall
+    time, sweeps, and the largest differences of J and of the gradient from the recorded
+    values, relative to the first point's J and gradient (J tends to 0 at an optimum).
+    Cold and warm replays do the same host work, so their times compare solver work."""
+    s = make_solver()
+    fg = gbo.make_fg(s, opts, opts, project=project, warm=warm)
+    J0, g0 = ref[0][0], float(ref[0][1].abs().max())
+    dJ = dg = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a, (J, g) in zip(pts, ref):
+        Jw, gw = fg(a)
+        if math.isfinite(J):
+            dJ = max(dJ, abs(Jw - J) / J0)
+            dg = max(dg, float((gw - g).abs().max()) / g0)
+    torch.cuda.synchronize()
+    res = {"s": time.perf_counter() - t0,
+           "sweeps": s.sweeps.get("primal_solve", 0) + s.sweeps.get("adjoint_solve", 0),
+           "max_diff_J_rel_J0": dJ, "max_diff_grad_rel_g0": dg}
+    s.close()
+    return res
+
+
 def time_to_gradient(torch, lbm, I, reps: int = 3):
     """Wall time of one gradient evaluation at fixed accuracy (primal to residual 1e-10,
     objective, adjoint to residual 1e-10, gradient) on the small workloads; min of reps.
@@ -379,10 +403,10 @@ def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 8000, seed: int
         out["time_to_gradient_%d" % nx] = agg
 
     # identification: distributed force on 512^2 towards the displacement of an 8-mode
-    # force.  L-BFGS runs cold and records its evaluation points; the warm-started solver
-    # then evaluates the same points (same objectives and gradients, each solve converged
-    # to the same residual), so both reach the same control error and only the solver
-    # time differs.  (A free-running warm L-BFGS follows a path that differs at rounding
+    # force.  L-BFGS runs cold and records its evaluation points; a cold and a
+    # warm-started solver then evaluate the same points (same objectives and gradients,
+    # each solve converged to the same residual), so both reach the same control error
+    # and only the solver time differs.  (A free-running warm L-BFGS follows a path that differs at rounding
     # level and takes a different number of steps; the replay isolates the warm start.)
     nx = 512
     Fstar = I.fourier_fields(1, nx, seed=21, kmax=4).reshape(-1).contiguous()
@@ -391,10 +415,15 @@ def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 8000, seed: int
     s.primal_solve(4_000_000, tol=1e-12, criterion=1, check_every=64)
     dstar = s.displacement()
     s.close()
+    opts = gbo.SolveOpts(tol=1e-10)
+
+    def solver():
+        s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu)
+        s.set_target(dstar)
+        return s
     pts, ref = [], []
-    s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu)
-    s.set_target(dstar)
-    fg = gbo.make_fg(s, gbo.SolveOpts(tol=1e-10), gbo.SolveOpts(tol=1e-10), project=True)
+    s = solver()
+    fg = gbo.make_fg(s, opts, opts, project=True)
 
     def rec(a):
         pts.append(a.detach().clone())
@@ -404,28 +433,14 @@ def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 8000, seed: int
     t0 = time.perf_counter()
     r = gbo.lbfgs(rec, torch.zeros_like(Fstar), m_max=6, eps=1e-14)
     torch.cuda.synchronize()
-    t_cold = time.perf_counter() - t0
+    t_run = time.perf_counter() - t0
+    s.close()
     err = float(torch.linalg.vector_norm(r.alpha - Fstar) / torch.linalg.vector_norm(Fstar))
     gres = {"controls": 2 * nx * nx, "lbfgs_steps": r.steps, "evaluations": len(pts),
-            "J": r.J, "control_rel_err": err,
-            "cold": {"s": t_cold, "sweeps": s.sweeps["primal_solve"] + s.sweeps["adjoint_solve"]}}
-    s.close()
-    s = lbm.LBMSolid(nx, nx, 1.0 / nx, E, nu)
-    s.set_target(dstar)
-    fgw = gbo.make_fg(s, gbo.SolveOpts(tol=1e-10), gbo.SolveOpts(tol=1e-10), project=True,
-                      warm=W.WarmStarter(nets["primal"], nets["adjoint"]))
-    dJ = dg = 0.0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for a, (J, g) in zip(pts, ref):
-        Jw, gw = fgw(a)
-        dJ = max(dJ, abs(Jw - J) / J)
-        dg = max(dg, float((gw - g).abs().max() / g.abs().max()))
-    torch.cuda.synchronize()
-    gres["warm"] = {"s": time.perf_counter() - t0,
-                    "sweeps": s.sweeps["primal_solve"] + s.sweeps["adjoint_solve"],
-                    "max_rel_diff_J": dJ, "max_rel_diff_grad": dg}
-    s.close()
+            "J": r.J, "control_rel_err": err, "lbfgs_run_s": t_run,
+            "cold": replay(torch, gbo, solver, pts, ref, opts, project=True),
+            "warm": replay(torch, gbo, solver, pts, ref, opts, project=True,
+                           warm=W.WarmStarter(nets["primal"], nets["adjoint"]))}
     gres["speedup"] = gres["cold"]["s"] / gres["warm"]["s"]
     out["identification_512"] = gres
     for w in nets.values():
@@ -438,7 +453,8 @@ def plate_identification(torch, lbm, I):
     state at E = 1): scalar E from E = 0.5 at N_x = 64, and a per-node modulus field from
     a uniform E = 0.5 towards a lognormal field (sigma 0.2) at N_x = 32.  L-BFGS runs cold
     (every solve from rest, as in the paper) and records its evaluation points; the same
-    points are then evaluated with every solve started from the history of steady states
+    points are then evaluated cold again and with every solve started from the history
+    of steady states
     (primal: last state, or for the scalar modulus the extrapolation in 1/E of the last
     three; adjoint: the previous adjoint states combined to fit the new source), so both
     runs reach the same control error and only the solver time differs.  The
@@ -460,7 +476,7 @@ def plate_identification(torch, lbm, I):
             s.set_control(torch.as_tensor(np.sqrt(Estar), device="cuda"))
             s.primal_solve(4_000_000, tol=1e-12, criterion=1, check_every=64)
             s.set_target(s.displacement())
-            s.sweeps["primal_solve"] = 0
+            s.sweeps.clear()
             return s
 
         opts = gbo.SolveOpts(tol=1e-10, max_steps=4_000_000)
@@ -481,7 +497,8 @@ def plate_identification(torch, lbm, I):
         t0 = time.perf_counter()
         r = gbo.lbfgs(rec, a0, m_max=m_max, eps=eps)
         torch.cuda.synchronize()
-        t_cold = time.perf_counter() - t0
+        t_run = time.perf_counter() - t0
+        s.close()
         act = torch.as_tensor(geo.active.astype(bool), device="cuda")
         E_got = (r.alpha ** 2)[act] if control == "young_field" else r.alpha ** 2
         E_ref = torch.as_tensor(Estar, device="cuda")[act] if control == "young_field" \
@@ -490,25 +507,9 @@ def plate_identification(torch, lbm, I):
                "evaluations": len(pts),
                "J0": r.history[0]["J"], "J": r.J,
                "modulus_rel_err": float((E_got - E_ref).abs().max() / E_ref.abs().max()),
-               "cold": {"s": t_cold, "sweeps": s.sweeps.get("primal_solve", 0) + s.sweeps.get("adjoint_solve", 0)}}
-        s.close()
-        s = solver()
-        fgw = gbo.make_fg(s, opts, opts, warm=W.WarmStarter(history=3))
-        # differences relative to the first point's J and gradient (J -> 0 at the optimum)
-        J0, g0 = ref[0][0], float(ref[0][1].abs().max())
-        dJ = dg = 0.0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for a, (J, g) in zip(pts, ref):
-            Jw, gw = fgw(a)
-            if math.isfinite(J):
-                dJ = max(dJ, abs(Jw - J) / J0)
-                dg = max(dg, float((gw - g).abs().max()) / g0)
-        torch.cuda.synchronize()
-        res["warm"] = {"s": time.perf_counter() - t0,
-                       "sweeps": s.sweeps.get("primal_solve", 0) + s.sweeps.get("adjoint_solve", 0),
-                       "max_diff_J_rel_J0": dJ, "max_diff_grad_rel_g0": dg}
-        s.close()
+               "lbfgs_run_s": t_run,
+               "cold": replay(torch, gbo, solver, pts, ref, opts),
+               "warm": replay(torch, gbo, solver, pts, ref, opts, warm=W.WarmStarter(history=3))}
         res["speedup"] = res["cold"]["s"] / res["warm"]["s"]
         out[name] = res
     return out
