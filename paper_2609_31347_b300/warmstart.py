@@ -305,7 +305,8 @@ class WarmStarter:
         kind = solver.control
         while len(entries) > 1:
             if kind == "young_scalar":
-                x = 1.0 / float(F[0]) ** 2
+                a = float(F[0])
+                x = 1.0 / (a * a) if a != 0.0 else math.inf
                 xs = [e[1] for e in entries]
                 if len(set(xs)) < len(xs) or not math.isfinite(x):
                     entries = entries[1:]
@@ -327,10 +328,9 @@ class WarmStarter:
         have_prev = self.reuse and bool(self.hist_f)
         if self.primal is None and not have_prev:
             return
-        N8 = 8 * solver.N
-        f0 = torch.empty(N8, dtype=torch.float64, device="cuda")
         if have_prev:
             entries, w = self._primal_weights(solver, F)
+            f0 = torch.empty_like(entries[-1][2])
             L.warm_combine(w, [e[2] for e in entries], f0)
             if self.primal is not None:
                 ref = torch.empty_like(F.reshape(-1))
@@ -338,6 +338,7 @@ class WarmStarter:
                 self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx, ref=ref,
                                     accumulate=True)
         else:
+            f0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
             self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx)
         solver.set_populations(0, f0)
 

@@ -143,3 +143,128 @@ def test_plate_adjoint_state_from_source_fit(plate):
     fit = np.abs(w[0] * P[Es[0]][0] + w[1] * P[Es[1]][0] - p_new).max()
     assert fit < 0.05 * reuse, (fit, reuse)
     assert fit < 0.05 * np.abs(p_new).max()
+
+
+# ---- WarmStarter's choices, with the library's two vector calls done in numpy ------
+
+class FakeSolver:
+    """Just what WarmStarter touches: control kind, geometry, the steady states."""
+
+    def __init__(self, control, periodic=False, N=5):
+        import torch
+        self.control, self.periodic, self.N, self.nx, self.dx = control, periodic, N, N, 1.0
+        self.f = torch.zeros(8 * N, dtype=torch.float64)
+        self.p = torch.zeros(8 * N, dtype=torch.float64)
+        self.r = torch.zeros(2 * N, dtype=torch.float64)
+        self.sets = []
+
+    def get_populations(self, which):
+        return self.f if which == 0 else self.p
+
+    def set_populations(self, which, t):
+        self.sets.append((which, t.clone()))
+
+    def adjoint_source(self):
+        return self.r.clone()
+
+
+@pytest.fixture
+def W(monkeypatch):
+    import torch
+    from paper_2609_31347_b300 import warmstart
+
+    def dots(vs):
+        V = torch.stack([v.reshape(-1) for v in vs]).numpy()
+        return V @ V.T
+
+    def combine(w, srcs, dst):
+        dst.copy_(sum(float(wi) * s for wi, s in zip(w, srcs)))
+        return dst
+
+    monkeypatch.setattr(warmstart.L, "warm_dots", dots)
+    monkeypatch.setattr(warmstart.L, "warm_combine", combine)
+    return warmstart
+
+
+def test_scalar_modulus_start_is_the_extrapolation_in_inverse_modulus(W):
+    import torch
+    rng = np.random.default_rng(3)
+    a, b, c = (torch.as_tensor(rng.standard_normal(40)) for _ in range(3))
+    state = lambda E: a + b / E + c / E ** 2  # quadratic in 1/E: reproduced exactly
+    s = FakeSolver("young_scalar")
+    ws = W.WarmStarter(history=3)
+    ctrl = lambda E: torch.tensor([np.sqrt(E)], dtype=torch.float64)
+    ws.before_primal(s, ctrl(0.5))
+    assert s.sets == []  # no history, no network: from rest
+    for E in (0.5, 0.8, 1.2):
+        s.f = state(E)
+        ws.after_primal(s, ctrl(E))
+    ws.before_primal(s, ctrl(1.0))
+    which, f0 = s.sets[-1]
+    assert which == 0
+    assert torch.allclose(f0, state(1.0), rtol=0, atol=1e-12)
+    # history = 1: the last state
+    ws1 = W.WarmStarter(history=1)
+    for E in (0.5, 0.8, 1.2):
+        s.f = state(E)
+        ws1.after_primal(s, ctrl(E))
+    ws1.before_primal(s, ctrl(1.0))
+    assert torch.equal(s.sets[-1][1], state(1.2))
+    # states crowded together and a far target: weights above the bound, so the
+    # oldest entries are dropped down to the last state
+    ws2 = W.WarmStarter(history=3)
+    for E in (1.0, 1.001, 1.002):
+        s.f = state(E)
+        ws2.after_primal(s, ctrl(E))
+    ws2.before_primal(s, ctrl(0.3))
+    assert torch.equal(s.sets[-1][1], state(1.002))
+
+
+def test_force_control_start_is_the_affine_fit(W):
+    import torch
+    rng = np.random.default_rng(4)
+    K = torch.as_tensor(rng.standard_normal((40, 10)))
+    f_of = lambda F: K @ F + 1.0  # steady state affine in the control
+    s = FakeSolver("force_field", periodic=True, N=5)
+    ws = W.WarmStarter(history=3)
+    x, d = torch.as_tensor(rng.standard_normal(10)), torch.as_tensor(rng.standard_normal(10))
+    for t in (0.0, 1.0, 0.4):  # points of one line search
+        s.f = f_of(x + t * d)
+        ws.after_primal(s, x + t * d)
+    ws.before_primal(s, x + 0.7 * d)
+    assert torch.allclose(s.sets[-1][1], f_of(x + 0.7 * d), rtol=0, atol=1e-11)
+
+
+def test_adjoint_start_fits_the_source_or_starts_from_rest(W):
+    import torch
+    rng = np.random.default_rng(5)
+    K = torch.as_tensor(rng.standard_normal((40, 10)))  # steady state linear in r
+    s = FakeSolver("young_scalar", N=5)
+    ws = W.WarmStarter(history=3)
+    R = [torch.as_tensor(rng.standard_normal(10)) for _ in range(2)]
+    ws.before_adjoint(s)
+    assert s.sets == []
+    for r in R:
+        s.r, s.p = r, K @ r
+        ws.before_adjoint(s)
+        ws.after_adjoint(s)
+    s.sets.clear()
+    s.r = 0.3 * R[0] - 0.7 * R[1]
+    ws.before_adjoint(s)
+    which, p0 = s.sets[-1]
+    assert which == 2
+    assert torch.allclose(p0, K @ s.r, rtol=0, atol=1e-12)
+    # a source the previous ones do not explain: from rest
+    s.sets.clear()
+    Q, _ = np.linalg.qr(np.stack([R[0].numpy(), R[1].numpy(), rng.standard_normal(10)], 1))
+    s.r = torch.as_tensor(Q[:, 2].copy())
+    ws.before_adjoint(s)
+    assert s.sets == []
+
+
+def test_networks_are_refused_off_the_periodic_force_field(W):
+    s = FakeSolver("young_scalar")
+    with pytest.raises(ValueError):
+        W.WarmStarter(primal=object()).before_primal(s, None)
+    with pytest.raises(ValueError):
+        W.WarmStarter(history=5)
