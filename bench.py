@@ -203,8 +203,8 @@ def time_to_gradient(torch, lbm, I, reps: int = 3):
     s.set_target(torch.as_tensor(c["dstar"].ravel(), device="cuda"))
     out["amplitudes_32"] = timed(s, torch.tensor([0.5, 0.25], dtype=torch.float64, device="cuda"), 2)
     s.close()
-    # distributed force control at half the reference force; 80^2 = 12,800 controls is the
-    # task's configuration, the others are the resolution ladder
+    # distributed force control at half the reference force; 80^2 (12,800 controls) is
+    # the distributed-control workload, the others are its resolution ladder
     for n in (20, 40, 80, 160):
         c = I.config_amplitudes(n)
         F = 0.5 * np.tensordot([1.0, 0.5], c["basis"], axes=1)
