@@ -55,3 +55,19 @@ def test_create_rejects_bad_descriptions_without_touching_the_device():
 
 def test_destroy_null_is_an_error_code():
     assert lbm.load_library().lbm_solid_destroy(None) == lbm.LBM_ERR_ARG
+
+
+def test_history_calls_reject_bad_arguments_without_touching_the_device():
+    lib = lbm.load_library()
+    assert lib.lbm_warm_dot_work_size() >= 15 * 296
+    w = (ctypes.c_double * 5)(1, 1, 1, 1, 1)
+    src = (ctypes.c_void_p * 5)(8, 8, 8, 8, 8)  # never dereferenced: rejected first
+    out = (ctypes.c_double * 36)()
+    for count, n in ((0, 10), (5, 10), (2, 0)):
+        assert lib.lbm_warm_combine(count, n, w, src, ctypes.c_void_p(8), None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_warm_combine(2, 10, None, src, ctypes.c_void_p(8), None) == lbm.LBM_ERR_ARG
+    src_null = (ctypes.c_void_p * 2)(8, None)
+    assert lib.lbm_warm_combine(2, 10, w, src_null, ctypes.c_void_p(8), None) == lbm.LBM_ERR_ARG
+    for m, n in ((0, 10), (6, 10), (3, 0)):
+        assert lib.lbm_warm_dots(m, n, src, ctypes.c_void_p(8), out, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_warm_dots(2, 10, src, None, out, None) == lbm.LBM_ERR_ARG
