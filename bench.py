@@ -335,9 +335,10 @@ def warm_start(torch, lbm, I, samples: int = 10000, steps: int = 8000, seed: int
     `samples` solver-generated 128^2 steady states each (random 8-mode fields), then
     iterations and wall time to residual 1e-10 cold vs warm on held-out 8-mode controls
     at 128^2 and 512^2 (the 128^2 networks used at 4x resolution), and an L-BFGS
-    identification of a distributed force on the 512^2 lattice: cold for a fixed number
-    of iterations, then warm (learned state of the control change added to the previous
-    steady state) until it reaches the same objective."""
+    identification of a distributed force on the 512^2 lattice: six L-BFGS steps run
+    cold and record their evaluation points, which are then replayed cold and warm
+    (starts combined from the loop's earlier steady states, plus the network's state of
+    the rest of the control change)."""
     from paper_2609_31347_b300 import gbo
     from paper_2609_31347_b300 import warmstart as W
     E, nu = 8.0 / 3.0, 1.0 / 3.0
