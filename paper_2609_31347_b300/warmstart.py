@@ -17,10 +17,12 @@ start"; this module orchestrates):
   (factor * nx)^2 lattices by block-averaging the input and interpolating the predicted
   moments, which are scaled so that they do not depend on the grid spacing.
 - ``WarmStarter``: supplies initial states to the solves of an optimisation loop.
-  Since the steady states are linear in F (primal) and in r (adjoint), the state of a
-  new control is the previous steady state plus the state of the change; with
-  ``reuse`` the network predicts only the change's state, so its error is relative to
-  the change, not to the whole state.
+  Since the steady states are affine in F (primal) and linear in r (adjoint), a
+  combination of the loop's earlier steady states reproduces the state of any control
+  (source) in the span of the earlier ones; the network then predicts only the state
+  of what is left of the change, so its error is relative to that remainder, not to
+  the whole state.  For a Young's-modulus control the primal states are extrapolated
+  in 1/E instead (no network).
 """
 from __future__ import annotations
 
