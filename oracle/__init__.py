@@ -26,13 +26,13 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (g++, -O2, no fast-math) into oracle/liblbm_oracle.so."""
+    """Compile the oracle (g++, -O2, OpenMP, no fast-math) into oracle/liblbm_oracle.so."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "lbm_oracle.h"))
     ):
         tmp = _LIB + ".tmp.%d" % os.getpid()
         subprocess.check_call(
-            ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math",
+            ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
              "-ffp-contract=off", "-o", tmp, _SRC]
         )
         os.replace(tmp, _LIB)
@@ -57,6 +57,10 @@ def _load():
             "orc_displacement": [P, P, P, P],
             "orc_stress": [P, P, P, P, P],
             "orc_monitor": [P, P, P, P],
+            "orc_primal_trace": [P, P, P, L, P],
+            "orc_adjoint_trace": [P, P, P, P, P, P, L, P],
+            "orc_set_threads": [I],
+            "orc_threads": [],
             "orc_apply_step": [P, P, P, P],
             "orc_apply_step_transpose": [P, P, P, P],
             "orc_adjoint": [P, P, P, P, P, P, L, P, P],
@@ -67,6 +71,8 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = I
+        lib.orc_cv_stop.argtypes = [P, L, L, D, P]
+        lib.orc_cv_stop.restype = L
         _lib = lib
     return _lib
 
@@ -258,6 +264,51 @@ def monitor(grid: Grid, fS, F):
     _check(_load().orc_monitor(ctypes.byref(cg), fS.ctypes.data, F.ctypes.data,
                                ctypes.addressof(c)), "monitor")
     return c.value
+
+
+def primal_trace(grid: Grid, E, F, steps: int):
+    """c(t) of Eq. (convergence) for t = 0 .. steps of the primal from rest, (steps+1,)."""
+    cg, keep = grid._c()
+    E, F = _E(grid, E), _arr(F, 2 * grid.N)
+    c = np.zeros(int(steps) + 1)
+    _check(_load().orc_primal_trace(ctypes.byref(cg), E.ctypes.data, F.ctypes.data,
+                                    int(steps), c.ctypes.data), "primal_trace")
+    return c
+
+
+def adjoint_trace(grid: Grid, E, F, fS, dstar, steps: int, obs=None):
+    """c of the adjoint displacement of phi_S(i), i = 0 .. steps, (steps+1,)."""
+    cg, keep = grid._c()
+    N = grid.N
+    E, F, fS, ds = _E(grid, E), _arr(F, 2 * N), _arr(fS, 8 * N), _arr(dstar, 2 * N)
+    ob = None if obs is None else _arr(obs, N)
+    c = np.zeros(int(steps) + 1)
+    _check(_load().orc_adjoint_trace(ctypes.byref(cg), E.ctypes.data, F.ctypes.data,
+                                     fS.ctypes.data, ds.ctypes.data,
+                                     None if ob is None else ob.ctypes.data, int(steps),
+                                     c.ctypes.data), "adjoint_trace")
+    return c
+
+
+def cv_stop(samples, window: int, tol: float):
+    """Eq. (convergence_crit) on a sample sequence: (first index where the trailing
+    window's std/mean < tol, or -1; last CV evaluated)."""
+    c = _arr(samples)
+    m = ctypes.c_double(float("nan"))
+    i = _load().orc_cv_stop(c.ctypes.data, c.size, int(window), float(tol), ctypes.addressof(m))
+    if i < -1:
+        raise ValueError("cv_stop: bad input")
+    return int(i), m.value
+
+
+def set_threads(n: int = 0) -> int:
+    """OpenMP threads of the oracle's node loops (0 = all processors); results do not
+    depend on it."""
+    return int(_load().orc_set_threads(int(n)))
+
+
+def threads() -> int:
+    return int(_load().orc_threads())
 
 
 def apply_step(grid: Grid, E, x):

@@ -1,7 +1,15 @@
 // CPU reference ("oracle") for the solid LBM of arXiv 2609.31347 -- TEST
 // INFRASTRUCTURE ONLY (see lbm_oracle.h).  Plain FP64, step by step in the order
 // of the paper; nothing here is blocked, fused or reordered for speed.
+//
+// Threads: loops whose iterations each write their own node (collision, gather
+// streaming, per-node setup) carry one OpenMP "parallel for"; every iteration does the
+// same arithmetic as in a serial run, so results do not depend on the thread count.
+// Sums (objective, Cbar, monitor) and the scatter of the transposed streaming on
+// bounded grids stay serial.
 #include "lbm_oracle.h"
+
+#include <omp.h>
 
 #include <cmath>
 #include <cstring>
@@ -204,16 +212,18 @@ bool make_ops(const Lat &L, const T *E, const T *Fx, const T *Fy, NodeOps<T> &op
   ops.gx.assign(L.N, T(0.0));
   ops.gy.assign(L.N, T(0.0));
   const double dx2 = L.dx * L.dx;
+  int bad = 0;
+#pragma omp parallel for reduction(| : bad)
   for (int n = 0; n < L.N; ++n) {
     if (!L.type[n]) continue;
-    if (!material(E[n], L.nu, ops.mat[n])) return false;
+    if (!material(E[n], L.nu, ops.mat[n])) { bad |= 1; continue; }
     const T gamma = (L.type[n] == 2) ? ops.mat[n].gamma_b : T(0.0);  // gamma = 0 in the bulk
     build_M(gamma, &ops.M[64 * (size_t)n]);
-    if (!invert8(&ops.M[64 * (size_t)n], &ops.Minv[64 * (size_t)n])) return false;
+    if (!invert8(&ops.M[64 * (size_t)n], &ops.Minv[64 * (size_t)n])) { bad |= 1; continue; }
     ops.gx[n] = T(dx2) * Fx[n];
     ops.gy[n] = T(dx2) * Fy[n];
   }
-  return true;
+  return bad == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -279,6 +289,8 @@ bool make_rules(const Lat &L, const NodeOps<T> &ops, std::vector<Rule<T>> &rules
   T M0[64], M0inv[64];
   build_M(T(0.0), M0);
   invert8(M0, M0inv);
+  int bad = 0;
+#pragma omp parallel for reduction(| : bad)
   for (int n = 0; n < N; ++n) {
     const int x = n % L.nx, y = n / L.nx;
     for (int k = 0; k < 8; ++k) {
@@ -320,17 +332,19 @@ bool make_rules(const Lat &L, const NodeOps<T> &ops, std::vector<Rule<T>> &rules
           r.coef[j] = T(2.0) * p[k] + T(j == kb ? -1.0 : 0.0);
         }
       } else {
-        return false;
+        bad |= 1;
       }
     }
   }
-  return true;
+  return bad == 0;
 }
 
 template <class T>
 void stream(const Lat &L, const std::vector<Rule<T>> &rules, const std::vector<T> &fC,
             std::vector<T> &fS, bool with_sources) {
-  for (size_t d = 0; d < rules.size(); ++d) {
+  const long nd = (long)rules.size();
+#pragma omp parallel for
+  for (long d = 0; d < nd; ++d) {
     const Rule<T> &r = rules[d];
     T s = with_sources ? r.cst : T(0.0);
     for (int t = 0; t < r.nterm; ++t) s += r.coef[t] * fC[r.src[t]];
@@ -339,11 +353,23 @@ void stream(const Lat &L, const std::vector<Rule<T>> &rules, const std::vector<T
   (void)L;
 }
 
-// Transposed streaming phi_S = S'^T phi_C (Eq. adjoint_streaming, S^-1 = S^T).
-void stream_T(const std::vector<Rule<double>> &rules, const std::vector<double> &phiC,
-              std::vector<double> &phiS) {
+// Transposed streaming phi_S = S'^T phi_C (Eq. adjoint_streaming, S^-1 = S^T).  On a
+// periodic lattice every rule is one term and the sources form a permutation, so the
+// scatter writes each entry once and runs in parallel; the boundary rules of a bounded
+// lattice add several terms into the same entries, so there it stays serial.
+void stream_T(const Lat &L, const std::vector<Rule<double>> &rules,
+              const std::vector<double> &phiC, std::vector<double> &phiS) {
   std::fill(phiS.begin(), phiS.end(), 0.0);
-  for (size_t d = 0; d < rules.size(); ++d) {
+  const long nd = (long)rules.size();
+  if (L.periodic) {
+#pragma omp parallel for
+    for (long d = 0; d < nd; ++d) {
+      const Rule<double> &r = rules[d];
+      for (int t = 0; t < r.nterm; ++t) phiS[r.src[t]] += r.coef[t] * phiC[d];
+    }
+    return;
+  }
+  for (long d = 0; d < nd; ++d) {
     const Rule<double> &r = rules[d];
     for (int t = 0; t < r.nterm; ++t) phiS[r.src[t]] += r.coef[t] * phiC[d];
   }
@@ -353,6 +379,7 @@ template <class T>
 void collide_all(const Lat &L, const NodeOps<T> &ops, const std::vector<T> &fS,
                  std::vector<T> &fC, bool with_force) {
   const int N = L.N;
+#pragma omp parallel for
   for (int n = 0; n < N; ++n) {
     if (!L.type[n]) {
       for (int k = 0; k < 8; ++k) fC[(size_t)k * N + n] = T(0.0);
@@ -366,9 +393,27 @@ void collide_all(const Lat &L, const NodeOps<T> &ops, const std::vector<T> &fS,
   }
 }
 
+// c of Eq. (convergence) for a displacement field given per node by disp(n, dx_, dy_):
+// the mean of |d_n|^2 over the active nodes.
+template <class Disp>
+double mean_sq_disp(const Lat &L, Disp disp) {
+  double s = 0.0;
+  for (int n = 0; n < L.N; ++n) {
+    if (!L.type[n]) continue;
+    double a, b;
+    disp(n, a, b);
+    s += a * a + b * b;
+  }
+  return L.n_active ? s / (double)L.n_active : 0.0;
+}
+
+template <class T>
+void node_disp(const Lat &L, const std::vector<T> &fS, int n, T gx, T gy, T &dx_, T &dy_);
+
+// trace (optional, steps + 1 values): c(t) of f_S(t) for t = 0 .. steps.
 template <class T>
 int run_primal(const Lat &L, const T *E, const T *Fx, const T *Fy, const double *fS0,
-               long steps, std::vector<T> &fS, std::vector<T> &fC) {
+               long steps, std::vector<T> &fS, std::vector<T> &fC, double *trace = nullptr) {
   NodeOps<T> ops;
   if (!make_ops(L, E, Fx, Fy, ops)) return -2;
   std::vector<Rule<T>> rules;
@@ -378,9 +423,19 @@ int run_primal(const Lat &L, const T *E, const T *Fx, const T *Fy, const double 
   fC.assign(P, T(0.0));
   if (fS0)
     for (size_t i = 0; i < P; ++i) fS[i] = T(fS0[i]);
+  auto c_of_state = [&]() {
+    return mean_sq_disp(L, [&](int n, double &a, double &b) {
+      T ta, tb;
+      node_disp(L, fS, n, ops.gx[n], ops.gy[n], ta, tb);
+      a = value(ta);
+      b = value(tb);
+    });
+  };
+  if (trace) trace[0] = c_of_state();
   for (long t = 0; t < steps; ++t) {
     collide_all(L, ops, fS, fC, true);  // f_C(t) = C[f_S(t), F]
     stream(L, rules, fC, fS, true);     // f_S(t+1) = S' f_C(t)
+    if (trace) trace[t + 1] = c_of_state();
   }
   return 0;
 }
@@ -422,6 +477,81 @@ T objective_of(const Lat &L, const std::vector<T> &fS, const T *Fx, const T *Fy,
     J += T(0.5 * w * dx2 / Cbar) * (ex * ex + ey * ey);  // Eqs. node_J, discrete_J
   }
   return J;
+}
+
+// Jacobian of one node's collision w.r.t. its populations, column j = C(e_j, g=0):
+// the collision is affine in f_S, so this is exact.
+void collision_jacobian(const NodeOps<double> &ops, int n, double A[64]) {
+  for (int j = 0; j < 8; ++j) {
+    double e[8] = {0, 0, 0, 0, 0, 0, 0, 0}, c[8];
+    e[j] = 1.0;
+    collide(e, 0.0, 0.0, ops.mat[n], &ops.M[64 * (size_t)n], &ops.Minv[64 * (size_t)n], c);
+    for (int r = 0; r < 8; ++r) A[r * 8 + j] = c[r];
+  }
+}
+
+// Algorithm 1.  trace (optional, steps + 1 values): c of Eq. (convergence) for the
+// adjoint displacement d^phi_n = (sum_k c_kx phi_S,k, sum_k c_ky phi_S,k) of
+// phi_S(i) = S'^T phi_C(i), i = 0 .. steps.
+int run_adjoint(const orc_grid *g, const double *E_node, const double *F, const double *fS,
+                const double *dstar, const double *obs, long steps, double *phiC_out,
+                double *phiS_out, double *trace) {
+  Lat L;
+  if (!make_lat(g, L) || !E_node || !F || !fS || !dstar || !phiC_out || !phiS_out || steps < 0)
+    return -1;
+  const int N = L.N;
+  const size_t P = 8 * (size_t)N;
+  NodeOps<double> ops;
+  if (!make_ops(L, E_node, F, F + N, ops)) return -2;
+  std::vector<Rule<double>> rules;
+  if (!make_rules(L, ops, rules)) return -3;
+  const double C = cbar_of(L, dstar, obs);
+  if (!(C > 0.0)) return -4;
+  // constant terms of Algorithm 1: A_n = dC_n/df and j = (dJ/df_S)^T at f_S
+  std::vector<double> A(64 * (size_t)N, 0.0), j(P, 0.0);
+  std::vector<double> f(fS, fS + P);
+  const double dx2 = L.dx * L.dx;
+#pragma omp parallel for
+  for (int n = 0; n < N; ++n) {
+    if (!L.type[n]) continue;
+    collision_jacobian(ops, n, &A[64 * (size_t)n]);
+    const double w = obs ? obs[n] : 1.0;
+    double dxn, dyn;
+    node_disp(L, f, n, ops.gx[n], ops.gy[n], dxn, dyn);
+    const double rx = w * dx2 / C * (dxn - dstar[n]);
+    const double ry = w * dx2 / C * (dyn - dstar[N + n]);
+    const double *M = &ops.M[64 * (size_t)n];
+    for (int k = 0; k < 8; ++k) j[(size_t)k * N + n] = rx * M[0 * 8 + k] + ry * M[1 * 8 + k];
+  }
+  std::vector<double> phiC(P, 0.0), phiS(P, 0.0);  // Eq. adjoint_init
+  auto c_of_phiS = [&]() {
+    return mean_sq_disp(L, [&](int n, double &a, double &b) {
+      a = b = 0.0;
+      for (int k = 0; k < 8; ++k) {
+        a += CX[k] * phiS[(size_t)k * N + n];
+        b += CY[k] * phiS[(size_t)k * N + n];
+      }
+    });
+  };
+  for (long it = 0; it < steps; ++it) {
+    stream_T(L, rules, phiC, phiS);  // Eq. adjoint_streaming
+    if (trace) trace[it] = c_of_phiS();
+#pragma omp parallel for
+    for (int n = 0; n < N; ++n) {  // Eq. adjoint_collision
+      if (!L.type[n]) continue;
+      const double *An = &A[64 * (size_t)n];
+      for (int c = 0; c < 8; ++c) {
+        double s = 0.0;
+        for (int r = 0; r < 8; ++r) s += An[r * 8 + c] * phiS[(size_t)r * N + n];
+        phiC[(size_t)c * N + n] = s - j[(size_t)c * N + n];
+      }
+    }
+  }
+  stream_T(L, rules, phiC, phiS);  // phi_S^inf = S^-1 phi_C^inf
+  if (trace) trace[steps] = c_of_phiS();
+  std::memcpy(phiC_out, phiC.data(), sizeof(double) * P);
+  std::memcpy(phiS_out, phiS.data(), sizeof(double) * P);
+  return 0;
 }
 
 }  // namespace
@@ -466,6 +596,38 @@ int orc_primal(const orc_grid *g, const double *E_node, const double *F, const d
   if (fC_out) std::memcpy(fC_out, fC.data(), sizeof(double) * fC.size());
   return 0;
 }
+
+int orc_primal_trace(const orc_grid *g, const double *E_node, const double *F, long steps,
+                     double *c_out) {
+  Lat L;
+  if (!make_lat(g, L) || !E_node || !F || !c_out || steps < 0) return -1;
+  std::vector<double> fS, fC;
+  return run_primal<double>(L, E_node, F, F + L.N, nullptr, steps, fS, fC, c_out);
+}
+
+long orc_cv_stop(const double *c, long n, long window, double tol, double *metric) {
+  if (!c || n < 0 || window < 2) return -2;
+  for (long i = window - 1; i < n; ++i) {
+    // the trailing window c[i - window + 1 .. i] (Eq. convergence_crit)
+    double mean = 0.0;
+    for (long j = i - window + 1; j <= i; ++j) mean += c[j];
+    mean /= (double)window;
+    double var = 0.0;
+    for (long j = i - window + 1; j <= i; ++j) var += (c[j] - mean) * (c[j] - mean);
+    const double sd = std::sqrt(var / (double)window);
+    const double cv = mean > 0.0 ? sd / mean : (sd == 0.0 ? 0.0 : INFINITY);
+    if (metric) *metric = cv;
+    if (cv < tol) return i;
+  }
+  return -1;
+}
+
+int orc_set_threads(int n) {
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+  return omp_get_max_threads();
+}
+
+int orc_threads(void) { return omp_get_max_threads(); }
 
 int orc_primal_tangent(const orc_grid *g, const double *E_node, const double *Edot,
                        const double *F, const double *Fdot, long steps, double *fS_out,
@@ -587,17 +749,6 @@ int orc_apply_step(const orc_grid *g, const double *E_node, const double *x, dou
   return 0;
 }
 
-// Jacobian of one node's collision w.r.t. its populations, column j = C(e_j, g=0):
-// the collision is affine in f_S, so this is exact.
-static void collision_jacobian(const NodeOps<double> &ops, int n, double A[64]) {
-  for (int j = 0; j < 8; ++j) {
-    double e[8] = {0, 0, 0, 0, 0, 0, 0, 0}, c[8];
-    e[j] = 1.0;
-    collide(e, 0.0, 0.0, ops.mat[n], &ops.M[64 * (size_t)n], &ops.Minv[64 * (size_t)n], c);
-    for (int r = 0; r < 8; ++r) A[r * 8 + j] = c[r];
-  }
-}
-
 int orc_apply_step_transpose(const orc_grid *g, const double *E_node, const double *y,
                              double *x) {
   Lat L;
@@ -609,7 +760,7 @@ int orc_apply_step_transpose(const orc_grid *g, const double *E_node, const doub
   if (!make_rules(L, ops, rules)) return -3;
   const size_t P = 8 * (size_t)L.N;
   std::vector<double> phiC(y, y + P), phiS(P);
-  stream_T(rules, phiC, phiS);
+  stream_T(L, rules, phiC, phiS);
   for (int n = 0; n < L.N; ++n) {
     for (int k = 0; k < 8; ++k) x[(size_t)k * L.N + n] = 0.0;
     if (!L.type[n]) continue;
@@ -627,49 +778,17 @@ int orc_apply_step_transpose(const orc_grid *g, const double *E_node, const doub
 int orc_adjoint(const orc_grid *g, const double *E_node, const double *F, const double *fS,
                 const double *dstar, const double *obs, long steps, double *phiC_out,
                 double *phiS_out) {
+  return run_adjoint(g, E_node, F, fS, dstar, obs, steps, phiC_out, phiS_out, nullptr);
+}
+
+int orc_adjoint_trace(const orc_grid *g, const double *E_node, const double *F,
+                      const double *fS, const double *dstar, const double *obs, long steps,
+                      double *c_out) {
+  if (!c_out) return -1;
   Lat L;
-  if (!make_lat(g, L) || !E_node || !F || !fS || !dstar || !phiC_out || !phiS_out || steps < 0)
-    return -1;
-  const int N = L.N;
-  const size_t P = 8 * (size_t)N;
-  NodeOps<double> ops;
-  if (!make_ops(L, E_node, F, F + N, ops)) return -2;
-  std::vector<Rule<double>> rules;
-  if (!make_rules(L, ops, rules)) return -3;
-  const double C = cbar_of(L, dstar, obs);
-  if (!(C > 0.0)) return -4;
-  // constant terms of Algorithm 1: A_n = dC_n/df and j = (dJ/df_S)^T at f_S
-  std::vector<double> A(64 * (size_t)N, 0.0), j(P, 0.0);
-  std::vector<double> f(fS, fS + P);
-  const double dx2 = L.dx * L.dx;
-  for (int n = 0; n < N; ++n) {
-    if (!L.type[n]) continue;
-    collision_jacobian(ops, n, &A[64 * (size_t)n]);
-    const double w = obs ? obs[n] : 1.0;
-    double dxn, dyn;
-    node_disp(L, f, n, ops.gx[n], ops.gy[n], dxn, dyn);
-    const double rx = w * dx2 / C * (dxn - dstar[n]);
-    const double ry = w * dx2 / C * (dyn - dstar[N + n]);
-    const double *M = &ops.M[64 * (size_t)n];
-    for (int k = 0; k < 8; ++k) j[(size_t)k * N + n] = rx * M[0 * 8 + k] + ry * M[1 * 8 + k];
-  }
-  std::vector<double> phiC(P, 0.0), phiS(P, 0.0);  // Eq. adjoint_init
-  for (long it = 0; it < steps; ++it) {
-    stream_T(rules, phiC, phiS);  // Eq. adjoint_streaming
-    for (int n = 0; n < N; ++n) {  // Eq. adjoint_collision
-      if (!L.type[n]) continue;
-      const double *An = &A[64 * (size_t)n];
-      for (int c = 0; c < 8; ++c) {
-        double s = 0.0;
-        for (int r = 0; r < 8; ++r) s += An[r * 8 + c] * phiS[(size_t)r * N + n];
-        phiC[(size_t)c * N + n] = s - j[(size_t)c * N + n];
-      }
-    }
-  }
-  stream_T(rules, phiC, phiS);  // phi_S^inf = S^-1 phi_C^inf
-  std::memcpy(phiC_out, phiC.data(), sizeof(double) * P);
-  std::memcpy(phiS_out, phiS.data(), sizeof(double) * P);
-  return 0;
+  if (!make_lat(g, L)) return -1;
+  std::vector<double> pc(8 * (size_t)L.N), ps(8 * (size_t)L.N);
+  return run_adjoint(g, E_node, F, fS, dstar, obs, steps, pc.data(), ps.data(), c_out);
 }
 
 int orc_gradient_force(const orc_grid *g, const double *E_node, const double *F,
@@ -684,6 +803,7 @@ int orc_gradient_force(const orc_grid *g, const double *E_node, const double *F,
   if (!(C > 0.0)) return -4;
   const double dx2 = L.dx * L.dx;
   std::vector<double> f(fS, fS + 8 * (size_t)N);
+#pragma omp parallel for
   for (int n = 0; n < N; ++n) {
     grad_out[n] = grad_out[N + n] = 0.0;
     if (!L.type[n]) continue;

@@ -91,6 +91,27 @@ int orc_stress(const orc_grid *g, const double *E_node, const double *fS, const 
                double *sigma_out);
 /* c(t) = (1/N_active) sum ||d_n||^2 (Eq. convergence). */
 int orc_monitor(const orc_grid *g, const double *fS, const double *F, double *c);
+/* c(t) of Eq. (convergence) for t = 0 .. steps of the primal from f_S(0) = 0:
+   c_out[t] = orc_monitor of f_S(t) (steps + 1 values). */
+int orc_primal_trace(const orc_grid *g, const double *E_node, const double *F, long steps,
+                     double *c_out);
+/* c of Eq. (convergence) for the adjoint displacement d^phi_n = (sum_k c_kx phi_S,k,
+   sum_k c_ky phi_S,k) of phi_S(i) = S'^T phi_C(i), i = 0 .. steps, along the iteration of
+   orc_adjoint (steps + 1 values). */
+int orc_adjoint_trace(const orc_grid *g, const double *E_node, const double *F,
+                      const double *fS, const double *dstar, const double *obs, long steps,
+                      double *c_out);
+/* Stopping rule of Eq. (convergence_crit) on a sequence of samples c[0..n): the first
+   index i >= window - 1 at which the trailing window c[i-window+1 .. i] has
+   std / mean < tol, with std the population standard deviation (divided by window)
+   and CV = 0 for a constant zero window; -1 if it never holds (-2 on bad input).
+   metric receives the last CV evaluated. */
+long orc_cv_stop(const double *c, long n, long window, double tol, double *metric);
+
+/* OpenMP threads of the node loops (n <= 0: all processors); returns the count in use.
+   Results do not depend on it. */
+int orc_set_threads(int n);
+int orc_threads(void);
 
 /* Homogeneous step operators for the dot-product identity:
    P x = S' L x (collide without force, stream without wall sources), and P^T y. */
