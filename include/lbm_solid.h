@@ -20,8 +20,24 @@
  *   - Populations are SoA: population k of node n at [k*N + n], k in the D2Q8 order
  *     Q = ((1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)), N = nx*ny.
  *     Two-component fields (force, displacement, gradient) are SoA [i*N + n].
- *   - All arithmetic is IEEE binary64; lattice units with dt = dx^2 (Section 3.1),
- *     lattice force g = dx^2 F.
+ *   - Storage is IEEE binary64 (populations, fields, controls, results); lattice
+ *     units with dt = dx^2 (Section 3.1), lattice force g = dx^2 F.
+ *   - Arithmetic of the sweeps (lbm_solid_desc.kernel):
+ *       LBM_KERNEL_FP64: every operation in binary64 (relative rounding 2^-53 per
+ *         operation).
+ *       LBM_KERNEL_AUTO (default): the collision of each bulk node (periodic nodes and
+ *         interior nodes of bounded grids; constant modulus) runs in 64-bit
+ *         fixed point scaled to the node's largest input: the ten inputs of the node (8
+ *         populations, 2 force or adjoint-source values) are converted to integers at
+ *         the scale 2^-56 of that largest input, combined exactly with integer adds and
+ *         62-bit fixed-point constants, and rounded back to binary64.  Every output is
+ *         within 4 * 2^-56 of the node's largest input of the exact value.  This is
+ *         tighter than binary64 for values near the node's maximum, but a value much
+ *         smaller than its node's maximum keeps fewer relative bits (a population 2^-40
+ *         of the node's largest input keeps about 16).  Nodes whose largest input lies
+ *         outside [2^-923, 2^57) (including all-zero nodes, Inf and NaN), boundary
+ *         nodes, per-node modulus fields, reductions, objectives and gradients use
+ *         binary64.
  *   - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA tensors) on
  *     the handle's device; *_host are host pointers; desc arrays are host arrays.
  *     All caller pointers are borrowed for the duration of the call only.
@@ -69,8 +85,8 @@ enum { LBM_LINK_REGULAR = 0, LBM_LINK_DIRICHLET = 1, LBM_LINK_NEUMANN = 2 };
 
 /* Arithmetic of the sweep kernels. */
 enum {
-  LBM_KERNEL_AUTO = 0, /* fastest variant that matches the FP64 reference       */
-  LBM_KERNEL_FP64 = 1  /* every operation on the FP64 pipe (strict binary64)     */
+  LBM_KERNEL_AUTO = 0, /* bulk collisions in 64-bit fixed point (see Conventions) */
+  LBM_KERNEL_FP64 = 1  /* every operation in binary64 on the FP64 pipe           */
 };
 
 typedef struct {
@@ -184,6 +200,17 @@ lbm_status lbm_solid_displacement(lbm_solid *h, double *d_dev);
 
 /* Number of kernel launches this handle has issued (for launch accounting). */
 long lbm_solid_launch_count(const lbm_solid *h);
+
+/* Monitor samples of the last primal or adjoint solve that used criterion 0 (Eqs.
+   convergence, convergence_crit), in order.  Sweeps run in chunks of check_every; a
+   chunk that ends after s >= 2 sweeps in total (and is not just the first sweep from an
+   explicit f_S) contributes one sample: c of Eq. (convergence) over the active nodes for
+   the state its last sweep collided, f_S(s - 1) for the primal and
+   phi_S(s - 1) = S'^T phi_C(s - 1) for the adjoint, whose displacement is
+   (sum_k c_kx phi_S,k, sum_k c_ky phi_S,k).  The stopping test is applied to these
+   samples.  Copies min(count, cap) values to dst_host (host, may be NULL) and returns
+   the count; -1 for a NULL handle. */
+long lbm_solid_monitor_samples(const lbm_solid *h, double *dst_host, long cap);
 
 /* ---- Batches of periodic lattices -------------------------------------------------
  * Many periodic instances of uneven size (e.g. independent identifications, or the
@@ -355,16 +382,25 @@ lbm_status lbm_warm_dots(int m, long n, const double *const *v_dev, double *work
  * allocate device memory, and so cannot create a handle (lbm_solid_create allocates).
  * Examples: a host application that gives all device memory to its own pool and
  * forbids other allocations, or a loop that must not pay the device-wide
- * synchronisation that cudaFree implies.  It computes the same J as
- * lbm_solid_objective (Eqs. node_J, discrete_J) from caller-owned device arrays and
- * calls no cudaMalloc, cudaFree or other allocating routine.
+ * synchronisation that cudaFree implies.  It computes the objective of a state from
+ * caller-owned device arrays and calls no cudaMalloc, cudaFree or other allocating
+ * routine:
+ *
+ *   J = (1/2) sum_n w_n |d_n - d*_n|^2 / sum_n w_n |d*_n|^2,  d_n = (m10 + dx^2 F_x / 2,
+ *       m01 + dx^2 F_y / 2) of the node's populations  (the dx^2 factors of the sum and
+ *       of its normalisation cancel),
+ *
+ * which is the value lbm_solid_objective returns for the same state, target and
+ * weights.  Every node of the nx x ny box is summed: on a bounded grid pass weights that
+ * are zero outside the domain (for instance the node mask as doubles), since the handle
+ * only sums the domain's nodes.
  *
  *   fS_dev    8N post-streaming populations, SoA [k*N + n] (e.g. from
  *             lbm_solid_get_populations(h, 0, ...))
- *   F_dev     2N physical body force (d = m10 + dx^2 F / 2, Eq. moments_bar_1/2)
- *   dstar_dev 2N target displacement;  obs_dev  N weights of Omega^J, or NULL = all 1
- *   J_dev     1 double, written with J = (1/2) sum obs |d - d*|^2 / sum obs |d*|^2
- *             (the dx^2 factors of J and Cbar cancel); NaN if the target has zero norm
+ *   F_dev     2N physical body force, SoA
+ *   dstar_dev 2N target displacement, SoA
+ *   obs_dev   N weights w_n, or NULL: w_n = 1 on every node of the box
+ *   J_dev     1 double, written with J; NaN if sum_n w_n |d*_n|^2 is zero
  *   stream    cudaStream_t the two kernels are enqueued on (NULL = legacy stream);
  *             the call returns without synchronising.
  *
@@ -373,11 +409,13 @@ lbm_status lbm_warm_dots(int m, long n, const double *const *v_dev, double *work
  * library holds until the process exits.  Grids with nx * ny > LBM_NOALLOC_MAX_NODES
  * are rejected with LBM_ERR_ARG before anything is launched.  The first call on each
  * device looks up that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture.  All calls on a device
- * share the array and every call rewrites the partials it reads, but calls that
- * overlap on the GPU (other streams, other host threads) race on it: serialise them.
- * Returns LBM_ERR_ARG for invalid sizes or NULL arrays, LBM_ERR_CUDA if the address
- * lookup or a launch fails. */
+ * current and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not call this entry point again on a device after
+ * cudaDeviceReset (the kept address then belongs to a destroyed context).  All calls on
+ * a device share the array and every call rewrites the partials it reads, but calls
+ * that overlap on the GPU (other streams, other host threads) race on it: serialise
+ * them.  Returns LBM_ERR_ARG for invalid sizes or NULL arrays, LBM_ERR_CUDA if the
+ * address lookup or a launch fails. */
 #define LBM_NOALLOC_MAX_NODES (1L << 20)
 lbm_status lbm_objective_noalloc(int nx, int ny, double dx, const double *fS_dev,
                                  const double *F_dev, const double *dstar_dev,

@@ -170,3 +170,73 @@ def mse_loss(y, t):
     """0.5 * mean((y - t)^2) and its gradient."""
     d = y - t
     return 0.5 * float(np.mean(d * d)), d / d.size
+
+
+# ---- the GPU's storage formats ------------------------------------------------------
+# The GPU network keeps weights, activations and gradients in BF16 and accumulates in
+# FP32.  The functions below run the same network with BF16 rounding applied exactly
+# where the GPU stores a tensor: the packed input, every convolution output (bias
+# included), every pooled and upsampled tensor, the output gradient and every input
+# gradient; the head output is FP32 and the weights are used in BF16.  Sums are taken in
+# FP64, so the GPU differs from these only by the order and width of its FP32 sums and
+# by the roundings that such a difference flips; an element-wise comparison can then use
+# a tolerance of a few BF16 units (2^-8) of each tensor's scale.
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def forward_formats(params, x, levels: int = 4, rnd=bf16):
+    """(y, acts, weights used) of the forward pass in the GPU's storage formats; rnd is
+    the rounding of stored tensors (identity gives forward() exactly)."""
+    pw = {k: (rnd(v) if k.endswith(".w") else v) for k, v in params.items()}
+    acts, skips = {}, []
+    h = rnd(x)
+    for l in range(levels):
+        for part in ("a", "b"):
+            name = "enc%d_%s" % (l, part)
+            acts[name] = h
+            h = rnd(conv(h, pw[name + ".w"], pw[name + ".b"]))
+        if l < levels - 1:
+            skips.append(h)
+            h = rnd(pool(h))
+    for l in range(levels - 2, -1, -1):
+        h = np.concatenate([rnd(up(h)), skips[l]], axis=3)
+        for part in ("a", "b"):
+            name = "dec%d_%s" % (l, part)
+            acts[name] = h
+            h = rnd(conv(h, pw[name + ".w"], pw[name + ".b"]))
+    acts["head"] = h
+    y = conv(h, pw["head.w"], pw["head.b"])
+    if rnd is bf16:
+        y = y.astype(np.float32).astype(np.float64)
+    return y, acts, pw
+
+
+def backward_formats(pw, acts, gy, levels: int = 4, rnd=bf16):
+    """Parameter gradients in the GPU's storage formats for the upstream gradient gy
+    (weights pw and activations acts from forward_formats)."""
+    grads = {}
+
+    def back(name, g):
+        gx, grads[name + ".w"], grads[name + ".b"] = conv_backward(acts[name], pw[name + ".w"], g)
+        return rnd(gx)
+
+    g = back("head", rnd(gy))
+    skip = {}
+    for l in range(levels - 1):
+        g = back("dec%d_b" % l, g)
+        g = back("dec%d_a" % l, g)
+        cu = pw["dec%d_a.w" % l].shape[2] - pw["dec%d_b.w" % l].shape[2]
+        skip[l] = g[..., cu:]
+        g = rnd(up_backward(g[..., :cu]))
+    for l in range(levels - 1, -1, -1):
+        if l < levels - 1:
+            g = rnd(pool_backward(g) + skip[l])
+        g = back("enc%d_b" % l, g)
+        g = back("enc%d_a" % l, g)
+    return grads

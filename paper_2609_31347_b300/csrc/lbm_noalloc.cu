@@ -4,6 +4,8 @@
 // array instead of handle-owned scratch.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "lbm_device.cuh"
 #include "lbm_solid.h"
 
@@ -16,7 +18,10 @@ constexpr long kMaxBlocks = LBM_NOALLOC_MAX_NODES / kThreads;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kMaxBlocks];
 
 constexpr int kMaxDevices = 64;
-static void *g_scratch_addr[kMaxDevices];  // device address of g_noalloc_scratch per device
+// Device address of g_noalloc_scratch per device, looked up on the first call on that
+// device.  Atomic: concurrent first calls from several host threads may both look it
+// up, and both store the same value.
+static std::atomic<void *> g_scratch_addr[kMaxDevices];
 
 // Per node: d = (m10 + dx^2 F_x / 2, m01 + dx^2 F_y / 2) of f_S; partial sums of
 // w |d - d*|^2 and w |d*|^2 for this block.
@@ -45,7 +50,8 @@ __global__ void __launch_bounds__(kThreads) k_objective_noalloc(
   }
 }
 
-// J = (1/2) sum w |d - d*|^2 dx^2 / (sum w |d*|^2 dx^2)  (Eqs. node_J, discrete_J).
+// J = (1/2) sum w |d - d*|^2 dx^2 / (sum w |d*|^2 dx^2), NaN when the weighted target
+// norm is zero.
 __global__ void __launch_bounds__(kThreads) k_objective_noalloc_finish(
     const double *__restrict__ scratch, long nb, double *__restrict__ J) {
   double acc[2] = {0.0, 0.0};
@@ -55,7 +61,8 @@ __global__ void __launch_bounds__(kThreads) k_objective_noalloc_finish(
   }
   __shared__ double sm[64];
   lbm::block_sum<2>(acc, sm);
-  if (threadIdx.x == 0) J[0] = 0.5 * acc[0] / acc[1];
+  if (threadIdx.x == 0)
+    J[0] = acc[1] != 0.0 ? 0.5 * acc[0] / acc[1] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 }  // namespace
@@ -71,14 +78,15 @@ extern "C" lbm_status lbm_objective_noalloc(int nx, int ny, double dx, const dou
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_ARG;
-  if (!g_scratch_addr[dev]) {
+  void *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
     // Host code cannot use the array's name as a device address: look it up once per
     // device, with that device current.
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LBM_ERR_CUDA;
-    g_scratch_addr[dev] = p;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr)
+      return LBM_ERR_CUDA;
+    g_scratch_addr[dev].store(addr, std::memory_order_release);
   }
-  double *scratch = static_cast<double *>(g_scratch_addr[dev]);
+  double *scratch = static_cast<double *>(addr);
   const long nb = (N + kThreads - 1) / kThreads;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_objective_noalloc<<<(unsigned)nb, kThreads, 0, s>>>(fS_dev, F_dev, dstar_dev, obs_dev, N,

@@ -70,6 +70,7 @@ struct lbm_solid {
   bool have_target = false, adjoint_valid = false, adj_warm = false;
   double cbar = 0.0;
   long launches = 0;
+  std::vector<double> samples;  // monitor samples c of the last criterion-0 solve
   bool broken = false;
   std::string err;
   dim3 blk, grd;
@@ -380,6 +381,7 @@ lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *inf
     steps = o->max_steps;
   } else {
     std::deque<double> win;
+    h->samples.clear();
     bool done = false;
     while (!done && steps < o->max_steps) {
       long k = o->check_every;
@@ -396,6 +398,7 @@ lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *inf
         if (st) return st;
         if ((st = fetch(h, 1))) return st;
         v = h->hres[0];
+        h->samples.push_back(v);
         if (!std::isfinite(v)) { metric = v; result = LBM_ERR_DIVERGED; break; }
         win.push_back(v);
         if ((long)win.size() > o->window) win.pop_front();
@@ -487,6 +490,14 @@ const char *lbm_status_string(lbm_status s) {
 const char *lbm_solid_last_error(const lbm_solid *h) { return h ? h->err.c_str() : "null handle"; }
 
 long lbm_solid_launch_count(const lbm_solid *h) { return h ? h->launches : -1; }
+
+long lbm_solid_monitor_samples(const lbm_solid *h, double *dst, long cap) {
+  if (!h) return -1;
+  const long n = (long)h->samples.size();
+  if (dst)
+    for (long i = 0; i < n && i < cap; ++i) dst[i] = h->samples[i];
+  return n;
+}
 
 lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **out) {
   if (!out || !d) return LBM_ERR_ARG;

@@ -37,6 +37,7 @@ EXPORTED = [
     "lbm_unet_set_params", "lbm_unet_forward", "lbm_unet_train_step", "lbm_unet_status",
     "lbm_solid_adjoint_source", "lbm_warm_encode", "lbm_warm_targets", "lbm_warm_decode", "lbm_warm_channel_rms",
     "lbm_warm_combine", "lbm_warm_dot_work_size", "lbm_warm_dots",
+    "lbm_solid_monitor_samples",
 ]
 
 
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_solid_set_populations": ([P, I, P], I),
         "lbm_solid_displacement": ([P, P], I),
         "lbm_solid_launch_count": ([P], ctypes.c_long),
+        "lbm_solid_monitor_samples": ([P, P, ctypes.c_long], ctypes.c_long),
         "lbm_status_string": ([I], ctypes.c_char_p),
         "lbm_solid_last_error": ([P], ctypes.c_char_p),
         "lbm_objective_noalloc": ([I, I, D, P, P, P, P, P, P], I),
@@ -258,6 +260,14 @@ class LBMSolid:
     @property
     def launch_count(self) -> int:
         return int(self._lib.lbm_solid_launch_count(self._h))
+
+    def monitor_samples(self) -> np.ndarray:
+        """Monitor samples c of the last criterion-0 solve (host array)."""
+        n = int(self._lib.lbm_solid_monitor_samples(self._h, None, 0))
+        out = np.zeros(max(n, 0))
+        if n > 0:
+            self._lib.lbm_solid_monitor_samples(self._h, out.ctypes.data, n)
+        return out
 
     @staticmethod
     def _opts(max_steps, tol, criterion, window, check_every, fixed_steps):

@@ -135,3 +135,41 @@ def test_batched_finite_difference_perturbations(lbm):
     fd = (J[0::2] - J[1::2]) / (2 * h)
     assert np.abs(fd - g[picks]).max() <= 1e-7 * np.abs(g).max()
     b.close()
+
+
+@pytest.mark.parametrize("kernel", ["fp64", "auto"])
+def test_batch_adjoint_and_gradient_match_the_oracle(lbm, kernel):
+    # uneven instances compared directly with the oracle: primal state, objective,
+    # adjoint phi_C (Eq. adjoint_iteration) and the nodal force gradient (Eq. optimality)
+    sizes = [(17, 9), (40, 23), (5, 31)]
+    E, nu, T, K = 0.7, 0.25, 41, 33
+    b = lbm.LBMBatch(sizes, E, nu, kernel=kernel)
+    Fb = np.zeros(2 * b.total)
+    Db = np.zeros(2 * b.total)
+    for i, (nx, ny) in enumerate(sizes):
+        o, n = b.offsets[i], nx * ny
+        Fb[2 * o:2 * (o + n)] = I.fourier_force(nx, ny=ny, seed=60 + i, kmax=2).ravel()
+        Db[2 * o:2 * (o + n)] = np.random.default_rng(70 + i).standard_normal(2 * n) * 1e-3
+    b.set_target(dev(Db))
+    b.set_force(dev(Fb))
+    b.primal(T)
+    Jb = host(b.objective())
+    b.adjoint(K)
+    fS, pC, gB = b.get_populations(0), b.get_populations(2), b.gradient()
+    for i, (nx, ny) in enumerate(sizes):
+        o, n = b.offsets[i], nx * ny
+        g = oracle.Grid(nx, ny, 1.0 / nx, nu)
+        F = Fb[2 * o:2 * (o + n)].reshape(2, n)
+        D = Db[2 * o:2 * (o + n)].reshape(2, n)
+        f_ref = oracle.primal(g, E, F, T)
+        J_ref, _ = oracle.objective(g, f_ref, F, D)
+        pc_ref, ps_ref = oracle.adjoint(g, E, F, f_ref, D, K)
+        g_ref = oracle.gradient_force(g, E, F, f_ref, ps_ref, D)
+        f_got = host(b.pop_view(fS, i))
+        assert np.abs(f_got - f_ref).max() <= 1e-11 * np.abs(f_ref).max(), i
+        assert abs(Jb[i] - J_ref) <= 1e-12 * abs(J_ref), i
+        p_got = host(b.pop_view(pC, i))
+        assert np.abs(p_got - pc_ref).max() <= 1e-11 * np.abs(pc_ref).max(), i
+        g_got = host(b.field_view(gB, i))
+        assert np.abs(g_got - g_ref).max() <= 1e-10 * np.abs(g_ref).max(), i
+    b.close()
