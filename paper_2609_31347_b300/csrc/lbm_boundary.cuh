@@ -15,7 +15,11 @@
 //     mbar_22 = -theta dx tr(sigma_w) / (4K) (pre-collision m22 streamed from
 //     m12^C = theta d, m21^C = theta d_y).
 // Each rule is evaluated on the unit vectors to give Q (8x8) and s (8) once per
-// material; the sweep kernels then apply f_S,k = sum_j Q_kj f_C,j(x) + s_k.
+// material (used by the tangent and gradient kernels), and in its compact form for the
+// sweeps: a rule depends on the node's own post-collision populations only through the
+// opposite population and the three relaxed moments (m11^C, m_s^C, m_d^C), so
+//   f_S,k = sigma_k f_C,kbar(x) + r_k0 m11^C + r_k1 m_s^C + r_k2 m_d^C + s_k,
+// sigma_k = +1 (Dirichlet) or -1 (Neumann), r_k = 0 for Dirichlet links.
 #pragma once
 #include "lbm_device.cuh"
 
@@ -49,14 +53,11 @@ struct Material {
   double dw11, dws, dwd, dK;
 };
 
+// 2 p of the Neumann rule from the node's relaxed post-collision moments.
 template <class T>
-__device__ inline void neumann_2p(const T (&fc)[8], T Tx, T Ty, double nx_, double ny_,
-                                  const T (&w)[3], T K, double dx, T (&p2)[8]) {
+__device__ inline void neumann_2p_m(T mc11, T mcs, T mcd, T Tx, T Ty, double nx_, double ny_,
+                                    const T (&w)[3], T K, double dx, T (&p2)[8]) {
   const T one(1.0), two(2.0), half(0.5);
-  // post-collision even moments of the node
-  const T mc11 = fc[4] - fc[5] + fc[6] - fc[7];
-  const T mcs = fc[0] + fc[1] + fc[2] + fc[3] + two * (fc[4] + fc[5] + fc[6] + fc[7]);
-  const T mcd = fc[0] - fc[1] + fc[2] - fc[3];
   const T b11 = mc11 * (two - w[0]) / (two * (one - w[0]));
   const T bs = mcs * (two - w[1]) / (two * (one - w[1]));
   const T bd = mcd * (two - w[2]) / (two * (one - w[2]));
@@ -76,6 +77,16 @@ __device__ inline void neumann_2p(const T (&fc)[8], T Tx, T Ty, double nx_, doub
   p2[1] = p2[3] = half * (ms - md) - m22;
   p2[4] = p2[6] = half * (m22 + m11);
   p2[5] = p2[7] = half * (m22 - m11);
+}
+
+template <class T>
+__device__ inline void neumann_2p(const T (&fc)[8], T Tx, T Ty, double nx_, double ny_,
+                                  const T (&w)[3], T K, double dx, T (&p2)[8]) {
+  // post-collision even moments of the node
+  const T mc11 = fc[4] - fc[5] + fc[6] - fc[7];
+  const T mcs = fc[0] + fc[1] + fc[2] + fc[3] + T(2.0) * (fc[4] + fc[5] + fc[6] + fc[7]);
+  const T mcd = fc[0] - fc[1] + fc[2] - fc[3];
+  neumann_2p_m(mc11, mcs, mcd, Tx, Ty, nx_, ny_, w, K, dx, p2);
 }
 
 template <class T>
@@ -116,11 +127,15 @@ __device__ inline Material material_of(double E, double nu) {
 // with respect to E (dQ, ds; skipped when dQ == nullptr).  With a modulus field
 // (alpha != nullptr) each record takes the material of its own node and also stores
 // its boundary gamma (Eq. gamma with tau_f = 1/2).
+// Compact form (R, dR: 4 doubles per link, SoA [(k*4 + i)*nb + b], i = 0..2 the
+// moment coefficients, i = 3 the constant s_k; dR their E-derivatives, skipped when
+// dR == nullptr).
 static __global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, long nb, Material m0,
                                  double dx, double *__restrict__ Q, double *__restrict__ s,
                                  double *__restrict__ dQ, double *__restrict__ ds,
                                  const double *__restrict__ alpha, const int *__restrict__ bnode,
-                                 double nu, double *__restrict__ gam) {
+                                 double nu, double *__restrict__ gam, double *__restrict__ R,
+                                 double *__restrict__ dR) {
   const long b = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const BoundaryNode bn = nodes[b];
@@ -134,6 +149,24 @@ static __global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, 
   const Dual w[3] = {Dual(m.w11, m.dw11), Dual(m.ws, m.dws), Dual(m.wd, m.dwd)};
   const Dual K(m.K, m.dK);
   for (int k = 0; k < 8; ++k) {
+    // compact form: moment coefficients of 2 p_k (Neumann) and the constant
+    Dual r[4];
+    if (bn.code[k] == 2) {
+      for (int i = 0; i < 3; ++i) {
+        Dual p2[8];
+        neumann_2p_m(Dual(i == 0 ? 1.0 : 0.0), Dual(i == 1 ? 1.0 : 0.0), Dual(i == 2 ? 1.0 : 0.0),
+                     Dual(0.0), Dual(0.0), bn.nrm[0], bn.nrm[1], w, K, dx, p2);
+        r[i] = p2[k];
+      }
+    }
+    if (bn.code[k] != 0) {
+      Dual zero[8];
+      r[3] = boundary_rule(bn, k, zero, true, w, K, dx);
+    }
+    for (int i = 0; i < 4; ++i) {
+      R[(long)(k * 4 + i) * nb + b] = r[i].v;
+      if (dR) dR[(long)(k * 4 + i) * nb + b] = r[i].d;
+    }
     if (bn.code[k] == 0) {
       s[b * 8 + k] = 0.0;
       if (dQ) ds[b * 8 + k] = 0.0;

@@ -51,10 +51,23 @@ struct Coef {
 // (m11, m_s, m_d) per node, gam the boundary gamma per boundary record.
 struct Field {
   const double *q;      // 3N: c11/4, cs/4, cd/4
+  const FixC *qfix;     // 3N: the same constants in fixed point (q11, qs, qd)
   const double *gam;    // nb
   const double *alpha;  // N: control, E_n = alpha_n^2
   double nu;
 };
+
+// Fixed-point collision constants of a node: the handle's, or the node's own planes of a
+// modulus field.
+template <bool FIELD>
+__device__ __forceinline__ CoefFix node_fix(const CoefFix &c, const Field &fl, long N, long n) {
+  if (!FIELD) return c;
+  CoefFix r = c;
+  r.q11 = fl.qfix[n];
+  r.qs = fl.qfix[N + n];
+  r.qd = fl.qfix[2 * N + n];
+  return r;
+}
 
 // The node's collision constants: the handle's for a uniform material, or the per-node
 // planes of a modulus field (boundary rows from the record's gamma).

@@ -24,8 +24,9 @@
 // largest biased exponent E lies in [kEmin, kEmax] (largest input between 2^-923 and
 // 2^57): then every shifted input keeps a positive exponent field, zeros and
 // subnormals shift to values below 1 that truncate to 0, and every nonzero result has
-// a normal exponent, so no per-value range test is needed.  Other nodes (all-zero
-// nodes, extreme magnitudes, Inf, NaN) take the FP64-pipe path.
+// a normal exponent, so no per-value range test is needed.  A node whose ten inputs are
+// all zero maps to zero (both maps are linear in their inputs), exactly; other nodes
+// (extreme magnitudes, subnormal-only nodes, Inf, NaN) take the FP64-pipe path.
 #pragma once
 #include "lbm_device.cuh"
 
@@ -83,6 +84,15 @@ __device__ __forceinline__ double from_fix(long long v, int E) {
   return __longlong_as_double(a == 0 ? 0ll : (long long)bits);
 }
 
+// True if all ten inputs are +0 or -0.
+__device__ __forceinline__ bool all_zero10(const double (&f)[8], double a, double b) {
+  int m = (__double2hiint(a) & 0x7fffffff) | __double2loint(a);
+  m |= (__double2hiint(b) & 0x7fffffff) | __double2loint(b);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) m |= (__double2hiint(f[k]) & 0x7fffffff) | __double2loint(f[k]);
+  return m == 0;
+}
+
 // Largest biased exponent of the node's ten inputs: the exponent field is monotone in
 // |x|, so take the max of the high words with the sign bit cleared, then extract once.
 __device__ __forceinline__ int max_exp10(const double (&f)[8], double a, double b) {
@@ -100,7 +110,13 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
                                             const CoefFix &c, double (&o)[8], double &dx_,
                                             double &dy_) {
   const int E = max_exp10(f, qx, qy);
-  if (E < kEmin || E > kEmax) return false;
+  if (E < kEmin || E > kEmax) {
+    if (E != 0 || !all_zero10(f, qx, qy)) return false;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = 0.0;
+    if (MON) dx_ = dy_ = 0.0;
+    return true;
+  }
   const int sh20 = (1079 - E) << 20;
   long long F[8];
 #pragma unroll
@@ -143,7 +159,13 @@ __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, d
                                               const CoefFix &c, double (&o)[8], double &ax,
                                               double &ay) {
   const int E = max_exp10(p, rx, ry);
-  if (E < kEmin || E > kEmax) return false;
+  if (E < kEmin || E > kEmax) {
+    if (E != 0 || !all_zero10(p, rx, ry)) return false;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = 0.0;
+    if (MON) ax = ay = 0.0;
+    return true;
+  }
   const int sh20 = (1079 - E) << 20;
   long long P[8];
 #pragma unroll

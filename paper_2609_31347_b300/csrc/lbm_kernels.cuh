@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(256) k_primal(const double *__restrict__ fin,
                                       (BOUNDED && FIELD && gsel != 0.0) ? b.bidx[n] : -1);
       if (BOUNDED && gsel != 0.0)
         collide<true>(f, qx, qy, c, o, dxn, dyn);
-      else if (ARITH == 0 || !collide_fix<MONITOR>(f, qx, qy, c.fx, o, dxn, dyn))
+      else if (ARITH == 0 ||
+               !collide_fix<MONITOR>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
         collide<false>(f, qx, qy, c, o, dxn, dyn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
@@ -215,7 +216,8 @@ __global__ void __launch_bounds__(256) k_collide_only(const double *__restrict__
   const double qx = g2[n], qy = g2[g.N + n];
   if (bnd)
     collide<true>(f, qx, qy, c, o, dxn, dyn);
-  else if (ARITH == 0 || !collide_fix<false>(f, qx, qy, c.fx, o, dxn, dyn))
+  else if (ARITH == 0 || !collide_fix<false>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o,
+                                             dxn, dyn))
     collide<false>(f, qx, qy, c, o, dxn, dyn);
 #pragma unroll
   for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
@@ -339,7 +341,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const double *__restrict__ pin,
                                       (BOUNDED && FIELD && gsel != 0.0) ? b.bidx[n] : -1);
       if (BOUNDED && gsel != 0.0)
         collide_T<true>(p, rx, ry, c, o, ax, ay);
-      else if (ARITH == 0 || !collide_T_fix<MONITOR>(p, rx, ry, c.fx, o, ax, ay))
+      else if (ARITH == 0 ||
+               !collide_T_fix<MONITOR>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
         collide_T<false>(p, rx, ry, c, o, ax, ay);
 #pragma unroll
       for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(256) k_grad_young(const double *__restrict__ f
 // Per-node collision constants of a modulus field: E_n = alpha_n^2 (Eq. E_substitution),
 // plane-stress moduli (Eqs. mu, K), relaxation (Table A.1, Eq. relaxation).
 static __global__ void k_set_young_field(const double *__restrict__ alpha, double nu, long N,
-                                  double *__restrict__ q) {
+                                  double *__restrict__ q, FixC *__restrict__ qfix) {
   for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N;
        n += (long)gridDim.x * blockDim.x) {
     const double E = alpha[n] * alpha[n];
@@ -482,6 +485,12 @@ static __global__ void k_set_young_field(const double *__restrict__ alpha, doubl
     q[n] = 0.25 * (1.0 - w11);
     q[N + n] = 0.25 * (1.0 - ws);
     q[2 * N + n] = 0.25 * (1.0 - wd);
+    // round(c 2^62) as hi 2^31 + lo, 0 <= lo < 2^31 (|c| < 1/2, so |C| < 2^61)
+    for (int i = 0; i < 3; ++i) {
+      const long long C = __double2ll_rn(q[i * N + n] * 4611686018427387904.0);
+      const long long hi = C >> 31;
+      qfix[i * N + n] = FixC{(int)hi, (int)(C - hi * 2147483648ll)};
+    }
   }
 }
 
@@ -621,6 +630,224 @@ __global__ void k_subtract_mean(double *__restrict__ v, const double *__restrict
   if (BOUNDED && b.type[n] == 0) return;
   v[n] -= mean[0];
   v[g.N + n] -= mean[1];
+}
+
+// ---------------------------------------------------------------------------------
+// Compact launch of a bounded grid.  The box is mostly outside the domain, and a warp
+// that holds one boundary node runs that node's rule and gamma-modified collision on
+// the FP64 pipe for all its lanes.  So the sweep launches only active nodes: first
+// kBndBlocks blocks of boundary nodes packed one per thread (they take longest, so
+// they start first), then the interior nodes as warp-sized chunks of up to 32
+// consecutive nodes of one row (every pull of such a warp is a contiguous, coalesced
+// access).  Interior nodes have all eight links regular.
+constexpr int kCompactThreads = 128;
+
+struct Compact {
+  const int2 *chunk;      // nchunk: (first node, count <= 32) of interior nodes of a row
+  const int *bnode;       // nb: node of boundary record b
+  const double *R;        // nb * 32: compact rules [(k*4 + i)*nb + b] (lbm_boundary.cuh)
+  const uint8_t *negmask; // nb: bit k set <=> missing link k is Neumann (sigma_k = -1)
+  long nchunk, nb;
+  int bblocks;            // blocks of boundary nodes (first in the grid)
+};
+
+// Missing-link populations of boundary record bi at node n from its own post-collision
+// populations own[] (compact rule form); regular links pulled as usual.
+__device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, long n,
+                                                const Grid &g, const Bounded &b,
+                                                const Compact &c, long bi,
+                                                double (&f)[8]) {
+  const unsigned reg = b.regmask[bi];
+  const unsigned neg = c.negmask[bi];
+  double own[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) own[j] = __ldg(fin + j * g.N + n);
+  const double mc11 = (own[4] - own[5]) + (own[6] - own[7]);
+  const double mcs = ((own[0] + own[1]) + (own[2] + own[3])) +
+                     2.0 * ((own[4] + own[5]) + (own[6] + own[7]));
+  const double mcd = (own[0] - own[1]) + (own[2] - own[3]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (reg & (1u << k)) {
+      f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+    } else {
+      const int kb = (k < 4) ? ((k + 2) & 3) : (((k - 4 + 2) & 3) + 4);
+      const double *r = c.R + (long)(k * 4) * c.nb + bi;
+      const double ob = (neg & (1u << k)) ? -own[kb] : own[kb];
+      f[k] = fma(__ldg(r), mc11, fma(__ldg(r + c.nb), mcs,
+                 fma(__ldg(r + 2 * c.nb), mcd, ob + __ldg(r + 3 * c.nb))));
+    }
+  }
+}
+
+// Transposed pull of boundary record bi: phi_S,j(x) = [link jbar regular] phi_C,j(x + c_j)
+// + sigma_jbar [link jbar missing] phi_C,jbar(x) + sum_i t_i dm_i/df_j, with
+// t_i = sum over missing links k of r_ki phi_C,k(x) (the transpose of pull_boundary_c).
+__device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ pin, long n,
+                                                    const Grid &g, const Bounded &b,
+                                                    const Compact &c, long bi,
+                                                    double (&p)[8]) {
+  const unsigned reg = b.regmask[bi];
+  const unsigned neg = c.negmask[bi];
+  double own[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) own[k] = __ldg(pin + k * g.N + n);
+  double t11 = 0.0, ts = 0.0, td = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!(reg & (1u << k))) {
+      const double *r = c.R + (long)(k * 4) * c.nb + bi;
+      t11 = fma(__ldg(r), own[k], t11);
+      ts = fma(__ldg(r + c.nb), own[k], ts);
+      td = fma(__ldg(r + 2 * c.nb), own[k], td);
+    }
+  }
+  const double ax = ts + td, ay = ts - td, d1 = 2.0 * ts + t11, d2 = 2.0 * ts - t11;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int jb = (j < 4) ? ((j + 2) & 3) : (((j - 4 + 2) & 3) + 4);
+    double acc;
+    if (reg & (1u << jb)) {
+      acc = __ldg(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx);
+    } else {
+      acc = (neg & (1u << jb)) ? -own[jb] : own[jb];
+    }
+    // dm11/df = (0,0,0,0,1,-1,1,-1), dms/df = (1,1,1,1,2,2,2,2), dmd/df = (1,-1,1,-1,0,..)
+    const double m = j < 4 ? ((j & 1) ? ay : ax) : ((j & 1) ? d2 : d1);
+    p[j] = acc + m;
+  }
+}
+
+// One primal sweep of a bounded grid (compact launch); monitor partial per block.
+template <bool MONITOR, int ARITH, bool FIELD>
+__global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__restrict__ fin,
+                                                              double *__restrict__ fout,
+                                                              const double *__restrict__ g2,
+                                                              Grid g, Bounded b, Compact c,
+                                                              Coef c0, Field fl,
+                                                              double *__restrict__ partial) {
+  double mon[1] = {0.0};
+  if ((int)blockIdx.x < c.bblocks) {
+    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    if (bi < c.nb) {
+      const long n = c.bnode[bi];
+      double f[8], o[8], dxn, dyn;
+      pull_boundary_c(fin, n, g, b, c, bi, f);
+      const Coef cc = node_coef<FIELD>(c0, fl, g.N, n, (int)bi);
+      collide<true>(f, __ldg(g2 + n), __ldg(g2 + g.N + n), cc, o, dxn, dyn);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
+      if (MONITOR) mon[0] = dxn * dxn + dyn * dyn;
+    }
+  } else {
+    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w < c.nchunk) {
+      const int2 ch = c.chunk[w];
+      if (lane < ch.y) {
+        const long n = (long)ch.x + lane;
+        double f[8], o[8], dxn = 0.0, dyn = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+        const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+        if (ARITH == 0 ||
+            !collide_fix<MONITOR>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
+          collide<false>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, -1), o, dxn, dyn);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
+        if (MONITOR) mon[0] = dxn * dxn + dyn * dyn;
+      }
+    }
+  }
+  if (MONITOR) {
+    __shared__ double sm[32];
+    block_sum<1>(mon, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = mon[0];
+  }
+}
+
+// One adjoint sweep of a bounded grid (compact launch).
+template <bool MONITOR, int ARITH, bool FIELD>
+__global__ void __launch_bounds__(kCompactThreads) k_adjoint_c(const double *__restrict__ pin,
+                                                               double *__restrict__ pout,
+                                                               const double *__restrict__ r,
+                                                               Grid g, Bounded b, Compact c,
+                                                               Coef c0, Field fl,
+                                                               double *__restrict__ partial) {
+  double mon[1] = {0.0};
+  if ((int)blockIdx.x < c.bblocks) {
+    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    if (bi < c.nb) {
+      const long n = c.bnode[bi];
+      double p[8], o[8], ax, ay;
+      pull_boundary_adj_c(pin, n, g, b, c, bi, p);
+      const Coef cc = node_coef<FIELD>(c0, fl, g.N, n, (int)bi);
+      collide_T<true>(p, __ldg(r + n), __ldg(r + g.N + n), cc, o, ax, ay);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
+      if (MONITOR) mon[0] = ax * ax + ay * ay;
+    }
+  } else {
+    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w < c.nchunk) {
+      const int2 ch = c.chunk[w];
+      if (lane < ch.y) {
+        const long n = (long)ch.x + lane;
+        double p[8], o[8], ax = 0.0, ay = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          p[k] = __ldg(pin + k * g.N + n + kCX[k] + (long)kCY[k] * g.nx);
+        const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
+        if (ARITH == 0 ||
+            !collide_T_fix<MONITOR>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
+          collide_T<false>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, -1), o, ax, ay);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
+        if (MONITOR) mon[0] = ax * ax + ay * ay;
+      }
+    }
+  }
+  if (MONITOR) {
+    __shared__ double sm[32];
+    block_sum<1>(mon, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = mon[0];
+  }
+}
+
+// Residual partials of a bounded grid over its active nodes only (compact launch):
+// max |a - b| and max |a| over the eight planes.
+static __global__ void __launch_bounds__(kCompactThreads) k_residual_c(
+    const double *__restrict__ a, const double *__restrict__ bb, Grid g, Compact c,
+    double *__restrict__ partial) {
+  double v[2] = {0.0, 0.0};
+  long n = -1;
+  if ((int)blockIdx.x < c.bblocks) {
+    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    if (bi < c.nb) n = c.bnode[bi];
+  } else {
+    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w < c.nchunk) {
+      const int2 ch = c.chunk[w];
+      if (lane < ch.y) n = (long)ch.x + lane;
+    }
+  }
+  if (n >= 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double ai = a[k * g.N + n];
+      v[0] = nan_max(v[0], fabs(ai - bb[k * g.N + n]));
+      v[1] = nan_max(v[1], fabs(ai));
+    }
+  }
+  __shared__ double sm[64];
+  block_max<2>(v, sm);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x * 2 + 0] = v[0];
+    partial[blockIdx.x * 2 + 1] = v[1];
+  }
 }
 
 // Residual partials: max |a - b| and max |a| over all planes.

@@ -42,7 +42,15 @@ struct lbm_solid {
   double alpha = 0.0;  // scalar Young control (E = alpha^2)
   // modulus field control: per-node constants, control copy, per-record gamma / node
   double *qfield = nullptr, *alphaN = nullptr, *gamf = nullptr;
+  FixC *qfix = nullptr;
   int *bnode = nullptr;
+  // compact launch of bounded grids: interior row chunks, boundary rules in compact form
+  Compact cmp{};
+  int2 *chunk = nullptr;
+  uint8_t *negmask = nullptr;
+  double *R = nullptr;
+  long cblocks = 0;
+  long nmon = 0;  // blocks that write monitor partials in a sweep
   Field fl{};
   bool field = false;
   // CUDA graphs of sweep chunks (launch overhead dominates small lattices): captured on
@@ -152,7 +160,7 @@ lbm_status setup_boundary(lbm_solid *h) {
   const unsigned blocks = (unsigned)((h->nb + threads - 1) / threads);
   k_boundary_setup<<<blocks, threads, 0, h->stream>>>(
       h->bnodes, h->nb, h->mat, h->dx, h->Q, h->s, h->dQ, h->ds, h->field ? h->alphaN : nullptr,
-      h->bnode, h->nu, h->gamf);
+      h->bnode, h->nu, h->gamf, h->R, nullptr);
   LAUNCHED(h);
   return LBM_OK;
 }
@@ -185,6 +193,7 @@ lbm_status fetch(lbm_solid *h, int nv) {
   return LBM_OK;
 }
 
+// Bounded grids launch their active nodes only (compact launch, lbm_kernels.cuh).
 template <int A, bool F>
 void launch_primal(lbm_solid *h, bool monitor) {
   if (h->periodic) {
@@ -193,10 +202,11 @@ void launch_primal(lbm_solid *h, bool monitor) {
     else
       k_primal<false, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl, nullptr);
   } else {
+    const unsigned nbk = (unsigned)h->cblocks;
     if (monitor)
-      k_primal<true, true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl, h->partial);
+      k_primal_c<true, A, F><<<nbk, kCompactThreads, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->cmp, h->coef, h->fl, h->partial);
     else
-      k_primal<true, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl, nullptr);
+      k_primal_c<false, A, F><<<nbk, kCompactThreads, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->cmp, h->coef, h->fl, nullptr);
   }
 }
 
@@ -208,10 +218,11 @@ void launch_adjoint(lbm_solid *h, bool monitor) {
     else
       k_adjoint<false, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->fl, nullptr);
   } else {
+    const unsigned nbk = (unsigned)h->cblocks;
     if (monitor)
-      k_adjoint<true, true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->fl, h->partial);
+      k_adjoint_c<true, A, F><<<nbk, kCompactThreads, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->cmp, h->coef, h->fl, h->partial);
     else
-      k_adjoint<true, false, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->coef, h->fl, nullptr);
+      k_adjoint_c<false, A, F><<<nbk, kCompactThreads, 0, h->stream>>>(h->pcur, h->pnext, h->r2, h->grid, h->bnd, h->cmp, h->coef, h->fl, nullptr);
   }
 }
 
@@ -223,23 +234,44 @@ void launch_collide_only(lbm_solid *h) {
     k_collide_only<true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl);
 }
 
-// One primal sweep; optional monitor partials (nblocks2d sums of |d|^2).  Arithmetic:
-// FP64 pipe for LBM_KERNEL_FP64 and for modulus fields, fixed point otherwise.
+// Kernel variant of a sweep: FP64 pipe for LBM_KERNEL_FP64, fixed-point bulk nodes
+// otherwise; per-node constants for modulus fields.
+void launch_primal_any(lbm_solid *h, bool monitor) {
+  const bool fp = h->kernel == LBM_KERNEL_FP64;
+  if (h->field) {
+    if (fp) launch_primal<0, true>(h, monitor);
+    else launch_primal<1, true>(h, monitor);
+  } else {
+    if (fp) launch_primal<0, false>(h, monitor);
+    else launch_primal<1, false>(h, monitor);
+  }
+}
+
+void launch_adjoint_any(lbm_solid *h, bool monitor) {
+  const bool fp = h->kernel == LBM_KERNEL_FP64;
+  if (h->field) {
+    if (fp) launch_adjoint<0, true>(h, monitor);
+    else launch_adjoint<1, true>(h, monitor);
+  } else {
+    if (fp) launch_adjoint<0, false>(h, monitor);
+    else launch_adjoint<1, false>(h, monitor);
+  }
+}
+
+// One primal sweep; optional monitor partials (nmon sums of |d|^2).
 lbm_status primal_sweep(lbm_solid *h, bool monitor) {
   const bool fp = h->kernel == LBM_KERNEL_FP64;
   if (h->fcur_is_fs) {
-    if (h->field)
-      launch_collide_only<0, true>(h);
-    else if (fp)
+    if (h->field) {
+      if (fp) launch_collide_only<0, true>(h);
+      else launch_collide_only<1, true>(h);
+    } else if (fp) {
       launch_collide_only<0, false>(h);
-    else
+    } else {
       launch_collide_only<1, false>(h);
-  } else if (h->field) {
-    launch_primal<0, true>(h, monitor);
-  } else if (fp) {
-    launch_primal<0, false>(h, monitor);
+    }
   } else {
-    launch_primal<1, false>(h, monitor);
+    launch_primal_any(h, monitor);
   }
   LAUNCHED(h);
   std::swap(h->fcur, h->fnext);
@@ -248,12 +280,7 @@ lbm_status primal_sweep(lbm_solid *h, bool monitor) {
 }
 
 lbm_status adjoint_sweep(lbm_solid *h, bool monitor) {
-  if (h->field)
-    launch_adjoint<0, true>(h, monitor);
-  else if (h->kernel == LBM_KERNEL_FP64)
-    launch_adjoint<0, false>(h, monitor);
-  else
-    launch_adjoint<1, false>(h, monitor);
+  launch_adjoint_any(h, monitor);
   LAUNCHED(h);
   std::swap(h->pcur, h->pnext);
   return LBM_OK;
@@ -283,14 +310,10 @@ lbm_status graph_for(lbm_solid *h, int kind, long k, bool mon, cudaGraphExec_t &
     // the kernels themselves (primal_sweep / adjoint_sweep without the launch check,
     // which would see the capture state)
     if (kind == 0) {
-      if (h->field) launch_primal<0, true>(h, m);
-      else if (h->kernel == LBM_KERNEL_FP64) launch_primal<0, false>(h, m);
-      else launch_primal<1, false>(h, m);
+      launch_primal_any(h, m);
       std::swap(h->fcur, h->fnext);
     } else {
-      if (h->field) launch_adjoint<0, true>(h, m);
-      else if (h->kernel == LBM_KERNEL_FP64) launch_adjoint<0, false>(h, m);
-      else launch_adjoint<1, false>(h, m);
+      launch_adjoint_any(h, m);
       std::swap(h->pcur, h->pnext);
     }
   }
@@ -348,16 +371,22 @@ lbm_status run_sweeps(lbm_solid *h, int kind, long k, bool mon) {
 }
 
 lbm_status set_field(lbm_solid *h) {
-  k_set_young_field<<<148 * 4, 256, 0, h->stream>>>(h->alphaN, h->nu, h->N, h->qfield);
+  k_set_young_field<<<148 * 4, 256, 0, h->stream>>>(h->alphaN, h->nu, h->N, h->qfield, h->qfix);
   LAUNCHED(h);
   return setup_boundary(h);
 }
 
 lbm_status residual(lbm_solid *h, const double *a, const double *b, double &res) {
-  const long total = 8 * h->N;
-  long blocks = (total + 255) / 256;
-  if (blocks > 148 * 8) blocks = 148 * 8;
-  k_residual<<<(unsigned)blocks, 256, 0, h->stream>>>(a, b, total, h->partial);
+  long blocks;
+  if (h->periodic) {
+    const long total = 8 * h->N;
+    blocks = (total + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    k_residual<<<(unsigned)blocks, 256, 0, h->stream>>>(a, b, total, h->partial);
+  } else {  // active nodes only
+    blocks = h->cblocks;
+    k_residual_c<<<(unsigned)blocks, kCompactThreads, 0, h->stream>>>(a, b, h->grid, h->cmp, h->partial);
+  }
   LAUNCHED(h);
   lbm_status st = finish(h, blocks, 2, 1, 1.0, h->dres);
   if (st) return st;
@@ -394,7 +423,7 @@ lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *inf
       if (steps < 2 || first_only) continue;
       double v = 0.0;
       if (o->criterion == 0) {
-        lbm_status st = finish(h, h->nblocks2d, 1, 0, h->n_active ? 1.0 / h->n_active : 0.0, h->dres);
+        lbm_status st = finish(h, h->nmon, 1, 0, h->n_active ? 1.0 / h->n_active : 0.0, h->dres);
         if (st) return st;
         if ((st = fetch(h, 1))) return st;
         v = h->hres[0];
@@ -464,7 +493,7 @@ void free_all(lbm_solid *h) {
   void *bufs[] = {h->fA, h->fB, h->pA, h->pB, h->g2, h->r2, h->dstar, h->obs, h->basis, h->Fbase,
                   h->type, h->regmask, h->bidx, h->Q, h->s, h->dQ, h->ds, h->bnodes,
                   h->partial, h->dres, h->qfield, h->alphaN, h->gamf, h->bnode, h->tA, h->tB,
-                  h->qdot};
+                  h->qdot, h->qfix, h->chunk, h->negmask, h->R};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (h->hres) cudaFreeHost(h->hres);
@@ -521,8 +550,9 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
   std::vector<uint8_t> type(N, 1);
   std::vector<int> bidx(N, -1);
   std::vector<BoundaryNode> bn;
-  std::vector<uint8_t> regm;
+  std::vector<uint8_t> regm, negm;
   std::vector<int> bnode_h;
+  std::vector<int2> chunks;
   if (h->periodic) {
     if (d->link_bc) return bail(LBM_ERR_ARG);
     if (d->node_mask)
@@ -539,7 +569,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
       ++h->n_active;
       const int x = (int)(n % d->nx), y = (int)(n / d->nx);
       BoundaryNode b{};
-      uint8_t reg = 0;
+      uint8_t reg = 0, neg = 0;
       bool any = false;
       for (int k = 0; k < 8; ++k) {
         const int xs = x - cx[k], ys = y - cy[k];
@@ -550,6 +580,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
         if (src_active != (code == 0)) return bail(LBM_ERR_ARG);
         b.code[k] = code;
         if (code == 0) reg |= (uint8_t)(1u << k);
+        if (code == 2) neg |= (uint8_t)(1u << k);
         if (code == 1) {
           if (!d->wall_d) return bail(LBM_ERR_ARG);
           b.wd[0] = d->wall_d[n]; b.wd[1] = d->wall_d[N + n];
@@ -567,10 +598,22 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
         bidx[n] = (int)bn.size();
         bn.push_back(b);
         regm.push_back(reg);
+        negm.push_back(neg);
         bnode_h.push_back((int)n);
       }
     }
     if (h->n_active == 0) return bail(LBM_ERR_ARG);
+    // interior nodes as chunks of up to 32 consecutive nodes of one row
+    for (int y = 0; y < d->ny; ++y) {
+      int x = 0;
+      while (x < d->nx) {
+        if (type[(long)y * d->nx + x] != 1) { ++x; continue; }
+        int e = x;
+        while (e < d->nx && e - x < 32 && type[(long)y * d->nx + e] == 1) ++e;
+        chunks.push_back(make_int2((int)((long)y * d->nx + x), e - x));
+        x = e;
+      }
+    }
   }
   h->nb = (long)bn.size();
 
@@ -588,7 +631,19 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
     h->grd = dim3((d->nx + h->blk.x - 1) / h->blk.x, (d->ny + h->blk.y - 1) / h->blk.y);
   }
   h->nblocks2d = (long)h->grd.x * h->grd.y;
-  h->partial_cap = 4 * (h->nblocks2d > 148 * 8 ? h->nblocks2d : 148 * 8);
+  h->nmon = h->nblocks2d;
+  if (!h->periodic) {
+    const long bblocks = (h->nb + kCompactThreads - 1) / kCompactThreads;
+    const long cw = kCompactThreads / 32;
+    h->cblocks = bblocks + ((long)chunks.size() + cw - 1) / cw;
+    h->nmon = h->cblocks;
+    h->cmp.nchunk = (long)chunks.size();
+    h->cmp.nb = h->nb;
+    h->cmp.bblocks = (int)bblocks;
+  }
+  long pmax = h->nblocks2d > h->cblocks ? h->nblocks2d : h->cblocks;
+  if (pmax < 148 * 8) pmax = 148 * 8;
+  h->partial_cap = 4 * pmax;
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes) \
   if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
@@ -602,17 +657,19 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
   h->field = d->control == LBM_CTRL_YOUNG_FIELD;
   if (h->field) {
     ALLOC(h->qfield, 3 * sizeof(double) * N);
+    ALLOC(h->qfix, 3 * sizeof(FixC) * N);
     ALLOC(h->alphaN, sizeof(double) * N);
-    if (!h->periodic && h->nb) {
-      ALLOC(h->gamf, sizeof(double) * h->nb);
-      ALLOC(h->bnode, sizeof(int) * h->nb);
-    }
+    if (!h->periodic && h->nb) ALLOC(h->gamf, sizeof(double) * h->nb);
   }
   if (!h->periodic) {
     ALLOC(h->type, N);
     ALLOC(h->bidx, sizeof(int) * N);
+    if (!chunks.empty()) ALLOC(h->chunk, sizeof(int2) * chunks.size());
     if (h->nb) {
       ALLOC(h->regmask, h->nb);
+      ALLOC(h->negmask, h->nb);
+      ALLOC(h->bnode, sizeof(int) * h->nb);
+      ALLOC(h->R, sizeof(double) * 32 * h->nb);
       ALLOC(h->bnodes, sizeof(BoundaryNode) * h->nb);
       ALLOC(h->Q, sizeof(double) * 64 * h->nb);
       ALLOC(h->s, sizeof(double) * 8 * h->nb);
@@ -645,10 +702,16 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
     up(h->bidx, bidx.data(), sizeof(int) * N);
     if (h->nb) {
       up(h->regmask, regm.data(), h->nb);
+      up(h->negmask, negm.data(), h->nb);
       up(h->bnodes, bn.data(), sizeof(BoundaryNode) * h->nb);
-      if (h->bnode) up(h->bnode, bnode_h.data(), sizeof(int) * h->nb);
+      up(h->bnode, bnode_h.data(), sizeof(int) * h->nb);
     }
+    if (!chunks.empty()) up(h->chunk, chunks.data(), sizeof(int2) * chunks.size());
     h->bnd = Bounded{h->type, h->bidx, h->Q, h->s, h->regmask, h->dQ, h->ds};
+    h->cmp.chunk = h->chunk;
+    h->cmp.bnode = h->bnode;
+    h->cmp.R = h->R;
+    h->cmp.negmask = h->negmask;
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->fA, 0, pop, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->fB, 0, pop, h->stream);
@@ -667,7 +730,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
     std::vector<double> a0(N, std::sqrt(d->E));
     up(h->alphaN, a0.data(), sizeof(double) * N);
     if (e != cudaSuccess) return bail(LBM_ERR_CUDA);
-    h->fl = Field{h->qfield, h->gamf, h->alphaN, h->nu};
+    h->fl = Field{h->qfield, h->qfix, h->gamf, h->alphaN, h->nu};
     if (set_field(h) != LBM_OK) return bail(LBM_ERR_CUDA);
   }
   if (h->Fbase) {
