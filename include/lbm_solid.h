@@ -251,9 +251,10 @@ lbm_status lbm_batch_gradient(lbm_batch *b, double *grad_dev);
 /* which = 0: f_S, 2: phi_C of every instance (8 * total values, device). */
 lbm_status lbm_batch_get_populations(lbm_batch *b, int which, double *dst_dev);
 /* Autotuner: times `sweeps` primal sweeps for tile widths 32, 64, 128 and 256 (tile =
-   width x 256/width nodes), keeps the fastest and restores the primal state.
-   best_bx (may be NULL) receives the chosen width.  Allocates one population-sized
-   scratch buffer for the duration of the call. */
+   width x 256/width nodes) and keeps the fastest, then does the same for the adjoint
+   sweep, which keeps its own width; the primal and adjoint states are restored.
+   best_bx (may be NULL) receives the primal sweep's width.  Allocates two
+   population-sized scratch buffers for the duration of the call. */
 lbm_status lbm_batch_tune(lbm_batch *b, int sweeps, int *best_bx);
 
 /* ---- Learned warm start ------------------------------------------------------------

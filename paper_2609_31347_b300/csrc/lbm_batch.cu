@@ -116,6 +116,32 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_batch(const double *__rest
   for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
 }
 
+// First adjoint sweep from rest: phi_C(1) = -j (the transposed collision of a zero
+// state, j_k = r . c_k), written without reading the zero state.
+__global__ void __launch_bounds__(kThreads) k_adjoint_rest_batch(const double *__restrict__ r,
+                                                                 double *__restrict__ pout,
+                                                                 const Inst *__restrict__ inst,
+                                                                 const int *__restrict__ blk_inst) {
+  const int ib = blk_inst[blockIdx.x];
+  const Inst I = inst[ib];
+  const long t = blockIdx.x - I.blk0;
+  const int x = (int)(t % I.tiles_x) * blockDim.x + threadIdx.x;
+  const int y = (int)(t / I.tiles_x) * blockDim.y + threadIdx.y;
+  if (x >= I.nx || y >= I.ny) return;
+  const long n = (long)y * I.nx + x;
+  const double rx = r[2 * I.off + n], ry = r[2 * I.off + I.N + n];
+  const double P1 = -rx - ry, P2 = rx - ry;
+  double *p = pout + 8 * I.off;
+  p[0 * I.N + n] = -rx;
+  p[1 * I.N + n] = -ry;
+  p[2 * I.N + n] = rx;
+  p[3 * I.N + n] = ry;
+  p[4 * I.N + n] = P1;
+  p[5 * I.N + n] = P2;
+  p[6 * I.N + n] = -P1;
+  p[7 * I.N + n] = -P2;
+}
+
 // Per block: sum |d - d*|^2 (objective) and write r = (dx^2/Cbar_i)(d - d*); or, with
 // dstar_only, sum |d*|^2 (Cbar).  Each block lies in one instance.
 __global__ void __launch_bounds__(kThreads) k_objective_batch(
@@ -239,6 +265,11 @@ struct lbm_batch {
   long nblocks = 0;
   Inst *d_inst = nullptr;
   int *d_blk = nullptr;
+  // the adjoint sweep's own tile width and block table (tuned separately)
+  int bx_a = 128;
+  long nblocks_a = 0;
+  Inst *d_inst_a = nullptr;
+  int *d_blk_a = nullptr;
   double *fA = nullptr, *fB = nullptr, *pA = nullptr, *pB = nullptr;
   double *q = nullptr, *r = nullptr, *dstar = nullptr;
   double *partial = nullptr, *cbar = nullptr, *rscale = nullptr, *jbuf = nullptr;
@@ -273,8 +304,9 @@ bool batch_coefs(double E, double nu, Coef &c) {
   return true;
 }
 
-// Block tables for tile width bx (blockDim = (bx, 256 / bx)).
-lbm_status build_tables(lbm_batch *b, int bx) {
+// Block tables for tile width bx (blockDim = (bx, 256 / bx)): which = 0 the table of the
+// primal sweep and of every other kernel, which = 1 the adjoint sweep's.
+lbm_status build_tables(lbm_batch *b, int which, int bx) {
   const int by = kThreads / bx;
   std::vector<Inst> inst(b->count);
   std::vector<int> blk;
@@ -286,12 +318,21 @@ lbm_status build_tables(lbm_batch *b, int bx) {
     blk0 += (long)tx * ty;
   }
   if (blk0 > 0x7fffffffL) return LBM_ERR_ARG;
-  if (b->d_blk) cudaFree(b->d_blk);
-  b->d_blk = nullptr;
-  if (cudaMalloc(&b->d_blk, sizeof(int) * blk.size()) != cudaSuccess) return LBM_ERR_OOM;
-  if (cudaMemcpy(b->d_blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_inst, inst.data(), sizeof(Inst) * b->count, cudaMemcpyHostToDevice) != cudaSuccess)
+  int *&d_blk = which == 0 ? b->d_blk : b->d_blk_a;
+  Inst *d_inst = which == 0 ? b->d_inst : b->d_inst_a;
+  if (d_blk) cudaFree(d_blk);
+  d_blk = nullptr;
+  if (cudaMalloc(&d_blk, sizeof(int) * blk.size()) != cudaSuccess) return LBM_ERR_OOM;
+  if (cudaMemcpy(d_blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_inst, inst.data(), sizeof(Inst) * b->count, cudaMemcpyHostToDevice) != cudaSuccess)
     return LBM_ERR_CUDA;
+  if (which == 1) {
+    b->nblocks_a = blk0;
+    b->bx_a = bx;
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    return LBM_OK;
+  }
   if (b->partial) cudaFree(b->partial);
   b->partial = nullptr;
   if (cudaMalloc(&b->partial, sizeof(double) * blk0) != cudaSuccess) return LBM_ERR_OOM;
@@ -314,10 +355,12 @@ void launch_sweep(lbm_batch *b, int kind, cudaStream_t s) {
       k_primal_batch<false, 1><<<g, bd, 0, s>>>(b->fcur, b->fnext, b->q, b->d_inst, b->d_blk, b->coef);
     std::swap(b->fcur, b->fnext);
   } else {
+    const dim3 ba(b->bx_a, kThreads / b->bx_a);
+    const unsigned ga = (unsigned)b->nblocks_a;
     if (b->kernel == LBM_KERNEL_FP64)
-      k_adjoint_batch<0><<<g, bd, 0, s>>>(b->pcur, b->pnext, b->r, b->d_inst, b->d_blk, b->coef);
+      k_adjoint_batch<0><<<ga, ba, 0, s>>>(b->pcur, b->pnext, b->r, b->d_inst_a, b->d_blk_a, b->coef);
     else
-      k_adjoint_batch<1><<<g, bd, 0, s>>>(b->pcur, b->pnext, b->r, b->d_inst, b->d_blk, b->coef);
+      k_adjoint_batch<1><<<ga, ba, 0, s>>>(b->pcur, b->pnext, b->r, b->d_inst_a, b->d_blk_a, b->coef);
     std::swap(b->pcur, b->pnext);
   }
 }
@@ -342,8 +385,9 @@ lbm_status run_batch_sweeps(lbm_batch *b, int kind, long k) {
     } else {
       const int parity = kind == 0 ? (b->fcur == b->fA ? 0 : 1) : (b->pcur == b->pA ? 0 : 1);
       cudaGraphExec_t ex = nullptr;
+      const int bxk = kind == 0 ? b->bx : b->bx_a;
       for (auto &g : b->graphs)
-        if (g.kind == kind && g.k == c && g.parity == parity && g.bx == b->bx) ex = g.exec;
+        if (g.kind == kind && g.k == c && g.parity == parity && g.bx == bxk) ex = g.exec;
       if (!ex) {
         if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
           return LBM_ERR_CUDA;
@@ -358,7 +402,7 @@ lbm_status run_batch_sweeps(lbm_batch *b, int kind, long k) {
         const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
         cudaGraphDestroy(graph);
         if (ei != cudaSuccess) return LBM_ERR_CUDA;
-        b->graphs.push_back(lbm_batch::G{kind, parity, b->bx, c, ex});
+        b->graphs.push_back(lbm_batch::G{kind, parity, bxk, c, ex});
       }
       if (cudaGraphLaunch(ex, b->stream) != cudaSuccess) return LBM_ERR_CUDA;
       if (c & 1) {
@@ -374,7 +418,7 @@ lbm_status run_batch_sweeps(lbm_batch *b, int kind, long k) {
 void free_batch(lbm_batch *b) {
   for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
   void *bufs[] = {b->d_inst, b->d_blk, b->fA, b->fB, b->pA, b->pB, b->q, b->r, b->dstar,
-                  b->partial, b->cbar, b->rscale, b->jbuf};
+                  b->partial, b->cbar, b->rscale, b->jbuf, b->d_inst_a, b->d_blk_a};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -414,6 +458,7 @@ lbm_status lbm_batch_create(int count, const int *nx, const int *ny, const doubl
 #define BALLOC(ptr, bytes) \
   if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
   BALLOC(b->d_inst, sizeof(Inst) * count);
+  BALLOC(b->d_inst_a, sizeof(Inst) * count);
   BALLOC(b->fA, pop); BALLOC(b->fB, pop); BALLOC(b->pA, pop); BALLOC(b->pB, pop);
   BALLOC(b->q, two); BALLOC(b->r, two); BALLOC(b->dstar, two);
   BALLOC(b->cbar, sizeof(double) * count); BALLOC(b->rscale, sizeof(double) * count);
@@ -424,7 +469,8 @@ lbm_status lbm_batch_create(int count, const int *nx, const int *ny, const doubl
     delete b;
     return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
   }
-  lbm_status st = build_tables(b, 128);
+  lbm_status st = build_tables(b, 0, 128);
+  if (st == LBM_OK) st = build_tables(b, 1, 128);
   if (st) { free_batch(b); delete b; return st; }
   if (cudaMemsetAsync(b->fA, 0, pop, b->stream) != cudaSuccess ||
       cudaMemsetAsync(b->pA, 0, pop, b->stream) != cudaSuccess ||
@@ -506,9 +552,16 @@ lbm_status lbm_batch_adjoint(lbm_batch *b, long sweeps) {
   if (!b->have_target) return LBM_ERR_STATE;
   const lbm_status st = lbm_batch_objective(b, b->jbuf);  // r at the current primal state
   if (st) return st;
-  if (cudaMemsetAsync(b->pcur, 0, sizeof(double) * 8 * b->total, b->stream) != cudaSuccess)
-    return LBM_ERR_CUDA;
-  const lbm_status s2 = run_batch_sweeps(b, 1, sweeps);
+  if (sweeps == 0) {  // phi_C = 0
+    if (cudaMemsetAsync(b->pcur, 0, sizeof(double) * 8 * b->total, b->stream) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  } else {  // from rest, the first sweep gives -j
+    k_adjoint_rest_batch<<<(unsigned)b->nblocks_a, dim3(b->bx_a, kThreads / b->bx_a), 0,
+                           b->stream>>>(b->r, b->pnext, b->d_inst_a, b->d_blk_a);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    std::swap(b->pcur, b->pnext);
+  }
+  const lbm_status s2 = run_batch_sweeps(b, 1, sweeps > 0 ? sweeps - 1 : 0);
   if (s2 == LBM_OK) b->adjoint_valid = true;
   return s2;
 }
@@ -549,46 +602,59 @@ lbm_status lbm_batch_get_populations(lbm_batch *b, int which, double *dst) {
 
 lbm_status lbm_batch_tune(lbm_batch *b, int sweeps, int *best_bx) {
   if (!b || sweeps < 1) return LBM_ERR_ARG;
-  // time `sweeps` primal sweeps for each tile width, keep the fastest (state restored)
+  // time `sweeps` primal sweeps, then `sweeps` adjoint sweeps, for each tile width and
+  // keep the fastest for each (both states restored)
   const int cands[] = {32, 64, 128, 256};
   const size_t pop = sizeof(double) * 8 * b->total;
-  double *save = nullptr;
+  double *save = nullptr, *save_p = nullptr;
   if (cudaMalloc(&save, pop) != cudaSuccess) return LBM_ERR_OOM;
-  if (cudaMemcpyAsync(save, b->fcur, pop, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) {
+  if (cudaMalloc(&save_p, pop) != cudaSuccess) {
     cudaFree(save);
+    return LBM_ERR_OOM;
+  }
+  if (cudaMemcpyAsync(save, b->fcur, pop, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(save_p, b->pcur, pop, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) {
+    cudaFree(save);
+    cudaFree(save_p);
     return LBM_ERR_CUDA;
   }
-  const bool was_fs = b->fs_explicit;
-  double *cur0 = b->fcur, *next0 = b->fnext;
+  const bool was_fs = b->fs_explicit, was_adj = b->adjoint_valid;
+  double *cur0 = b->fcur, *next0 = b->fnext, *pcur0 = b->pcur, *pnext0 = b->pnext;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int bestbx = b->bx;
+  int best_w[2] = {b->bx, b->bx_a};
   lbm_status st = LBM_OK;
-  for (int bx : cands) {
-    if ((st = build_tables(b, bx))) break;
-    b->fs_explicit = false;
-    run_batch_sweeps(b, 0, 4);  // capture + warm-up
-    cudaEventRecord(e0, b->stream);
-    run_batch_sweeps(b, 0, sweeps);
-    cudaEventRecord(e1, b->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; bestbx = bx; }
+  for (int kind = 0; kind < 2 && st == LBM_OK; ++kind) {
+    float best = 1e30f;
+    for (int bx : cands) {
+      if ((st = build_tables(b, kind, bx))) break;
+      b->fs_explicit = false;
+      run_batch_sweeps(b, kind, 4);  // capture + warm-up
+      cudaEventRecord(e0, b->stream);
+      run_batch_sweeps(b, kind, sweeps);
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_w[kind] = bx; }
+    }
+    if (st == LBM_OK) st = build_tables(b, kind, best_w[kind]);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st == LBM_OK) st = build_tables(b, bestbx);
   b->fcur = cur0;
   b->fnext = next0;
+  b->pcur = pcur0;
+  b->pnext = pnext0;
   cudaMemcpyAsync(b->fcur, save, pop, cudaMemcpyDeviceToDevice, b->stream);
+  cudaMemcpyAsync(b->pcur, save_p, pop, cudaMemcpyDeviceToDevice, b->stream);
   cudaStreamSynchronize(b->stream);
   cudaFree(save);
+  cudaFree(save_p);
   b->fs_explicit = was_fs;
-  b->adjoint_valid = false;
-  if (best_bx) *best_bx = bestbx;
+  b->adjoint_valid = was_adj;
+  if (best_bx) *best_bx = best_w[0];
   return st;
 }
 

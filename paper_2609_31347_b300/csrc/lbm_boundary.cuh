@@ -135,7 +135,8 @@ static __global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, 
                                  double *__restrict__ dQ, double *__restrict__ ds,
                                  const double *__restrict__ alpha, const int *__restrict__ bnode,
                                  double nu, double *__restrict__ gam, double *__restrict__ R,
-                                 double *__restrict__ dR) {
+                                 double *__restrict__ dR, FixC *__restrict__ bfix,
+                                 uint8_t *__restrict__ bok) {
   const long b = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const BoundaryNode bn = nodes[b];
@@ -144,7 +145,15 @@ static __global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, 
     const double a = alpha[bnode[b]];
     m = material_of(a * a, nu);
     const double ts = 1.0 / m.ws - 0.5;
-    gam[b] = kTheta * 0.5 / ((1.0 + kTheta) * (ts - 0.5));
+    const double gm = kTheta * 0.5 / ((1.0 + kTheta) * (ts - 0.5));
+    gam[b] = gm;
+    // the record's gamma-modified collision constants in fixed point, when below 1/2
+    const double cs = 1.0 - m.ws;
+    const double qs_b = cs * (0.25 + 0.5 * gm), P_b = -0.25 * gm * cs;
+    const bool ok = fabs(qs_b) < 0.499 && fabs(P_b) < 0.499;
+    bfix[2 * b] = ok ? fixc_of(qs_b) : FixC{0, 0};
+    bfix[2 * b + 1] = ok ? fixc_of(P_b) : FixC{0, 0};
+    bok[b] = ok ? 1 : 0;
   }
   const Dual w[3] = {Dual(m.w11, m.dw11), Dual(m.ws, m.dws), Dual(m.wd, m.dwd)};
   const Dual K(m.K, m.dK);

@@ -32,6 +32,8 @@ struct FixC {
 
 struct CoefFix {
   FixC qs, qd, q11, third;  // cs/4, cd/4, c11/4, 1/3
+  FixC qs_b, P_b;           // boundary rows: cs (1/4 + gamma/2), -gamma cs / 4
+  int bnd_ok;               // the boundary constants are below 1/2 in magnitude
 };
 
 // Per-material constants (host-computed, passed by value).
@@ -53,9 +55,18 @@ struct Field {
   const double *q;      // 3N: c11/4, cs/4, cd/4
   const FixC *qfix;     // 3N: the same constants in fixed point (q11, qs, qd)
   const double *gam;    // nb
+  const FixC *bfix;     // 2 nb: qs_b, P_b of each boundary record in fixed point
+  const uint8_t *bok;   // nb: those are below 1/2 in magnitude
   const double *alpha;  // N: control, E_n = alpha_n^2
   double nu;
 };
+
+// c -> round(c 2^62) as hi 2^31 + lo, 0 <= lo < 2^31 (|c| < 1/2).
+__device__ __forceinline__ FixC fixc_of(double c) {
+  const long long C = __double2ll_rn(c * 4611686018427387904.0);
+  const long long hi = C >> 31;
+  return FixC{(int)hi, (int)(C - hi * 2147483648ll)};
+}
 
 // Fixed-point collision constants of a node: the handle's, or the node's own planes of a
 // modulus field.
@@ -68,6 +79,20 @@ __device__ __forceinline__ CoefFix node_fix(const CoefFix &c, const Field &fl, l
   r.qd = fl.qfix[2 * N + n];
   return r;
 }
+
+// The same for boundary record bi (its gamma-modified rows); false when the record's
+// constants are too large for the fixed-point path.
+template <bool FIELD>
+__device__ __forceinline__ bool node_fix_bnd(const CoefFix &c, const Field &fl, long N, long n,
+                                             long bi, CoefFix &r) {
+  r = node_fix<FIELD>(c, fl, N, n);
+  if (!FIELD) return c.bnd_ok != 0;
+  if (!fl.bok[bi]) return false;
+  r.qs_b = fl.bfix[2 * bi];
+  r.P_b = fl.bfix[2 * bi + 1];
+  return true;
+}
+
 
 // The node's collision constants: the handle's for a uniform material, or the per-node
 // planes of a modulus field (boundary rows from the record's gamma).

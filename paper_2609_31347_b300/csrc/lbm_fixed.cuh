@@ -84,13 +84,19 @@ __device__ __forceinline__ double from_fix(long long v, int E) {
   return __longlong_as_double(a == 0 ? 0ll : (long long)bits);
 }
 
-// True if all ten inputs are +0 or -0.
-__device__ __forceinline__ bool all_zero10(const double (&f)[8], double a, double b) {
+// A node whose ten inputs are all +0 or -0 maps to zero (the collision and its transpose
+// are linear): writes zeros and returns true, else returns false.  Tried only on nodes
+// that the fixed-point path declined, before the FP64-pipe path.
+__device__ __forceinline__ bool zero_node(const double (&f)[8], double a, double b,
+                                          double (&o)[8]) {
   int m = (__double2hiint(a) & 0x7fffffff) | __double2loint(a);
   m |= (__double2hiint(b) & 0x7fffffff) | __double2loint(b);
 #pragma unroll
   for (int k = 0; k < 8; ++k) m |= (__double2hiint(f[k]) & 0x7fffffff) | __double2loint(f[k]);
-  return m == 0;
+  if (m != 0) return false;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) o[k] = 0.0;
+  return true;
 }
 
 // Largest biased exponent of the node's ten inputs: the exponent field is monotone in
@@ -103,20 +109,15 @@ __device__ __forceinline__ int max_exp10(const double (&f)[8], double a, double 
   return m >> 20;
 }
 
-// Bulk collision in fixed point (same map as collide<false>).  Returns false when the
-// node must take the FP64-pipe path (largest exponent outside [kEmin, kEmax]).
-template <bool MON>
+// Collision in fixed point (same map as collide<BND>; boundary rows use qs_b, P_b).
+// Returns false when the node must take the FP64-pipe path (largest exponent outside
+// [kEmin, kEmax]).
+template <bool MON, bool BND = false>
 __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, double qy,
                                             const CoefFix &c, double (&o)[8], double &dx_,
                                             double &dy_) {
   const int E = max_exp10(f, qx, qy);
-  if (E < kEmin || E > kEmax) {
-    if (E != 0 || !all_zero10(f, qx, qy)) return false;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = 0.0;
-    if (MON) dx_ = dy_ = 0.0;
-    return true;
-  }
+  if (E < kEmin || E > kEmax) return false;
   const int sh20 = (1079 - E) << 20;
   long long F[8];
 #pragma unroll
@@ -131,7 +132,7 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
   const long long m11 = a3 - a4;
   const long long ms = a1 + a2 + 2 * (a3 + a4);
   const long long md = a1 - a2;
-  const long long es = mulfix(ms, c.qs);
+  const long long es = mulfix(ms, BND ? c.qs_b : c.qs);
   const long long td = mulfix(md, c.qd);
   const long long e1 = es + td, e2 = es - td;
   const long long t10 = mulfix(mb10, c.third), t01 = mulfix(mb01, c.third);
@@ -142,10 +143,18 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
   o[2] = from_fix(e1 - o1, E);
   o[1] = from_fix(e2 + o2, E);
   o[3] = from_fix(e2 - o2, E);
-  o[4] = from_fix(q11 + u, E);
-  o[6] = from_fix(q11 - u, E);
-  o[5] = from_fix(v - q11, E);
-  o[7] = from_fix(-q11 - v, E);
+  if (BND) {
+    const long long P = mulfix(ms, c.P_b);  // m22^C / 4 = -gamma m_s^C / 4
+    o[4] = from_fix((P + q11) + u, E);
+    o[6] = from_fix((P + q11) - u, E);
+    o[5] = from_fix((P - q11) + v, E);
+    o[7] = from_fix((P - q11) - v, E);
+  } else {
+    o[4] = from_fix(q11 + u, E);
+    o[6] = from_fix(q11 - u, E);
+    o[5] = from_fix(v - q11, E);
+    o[7] = from_fix(-q11 - v, E);
+  }
   if (MON) {
     dx_ = from_fix(mb10, E);
     dy_ = from_fix(mb01, E);
@@ -153,19 +162,13 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
   return true;
 }
 
-// Bulk transposed collision in fixed point (same map as collide_T<false>).
-template <bool MON>
+// Transposed collision in fixed point (same map as collide_T<BND>).
+template <bool MON, bool BND = false>
 __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, double ry,
                                               const CoefFix &c, double (&o)[8], double &ax,
                                               double &ay) {
   const int E = max_exp10(p, rx, ry);
-  if (E < kEmin || E > kEmax) {
-    if (E != 0 || !all_zero10(p, rx, ry)) return false;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = 0.0;
-    if (MON) ax = ay = 0.0;
-    return true;
-  }
+  if (E < kEmin || E > kEmax) return false;
   const int sh20 = (1079 - E) << 20;
   long long P[8];
 #pragma unroll
@@ -180,7 +183,9 @@ __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, d
   const long long n10 = mulfix(B1 + (d34 >> 2), c.third) - RX;
   const long long n01 = mulfix(B2 + (s34 >> 2), c.third) - RY;
   const long long n11 = mulfix(A3 - A4, c.q11);
-  const long long ns = mulfix(A1 + A2, c.qs);
+  // d/dm_s of the outputs: cs (1/4 + gamma/2) on axis pairs, -gamma cs / 4 on diagonals
+  const long long ns = BND ? mulfix(A1 + A2, c.qs_b) + mulfix(A3 + A4, c.P_b)
+                           : mulfix(A1 + A2, c.qs);
   const long long nd = mulfix(A1 - A2, c.qd);
   const long long S1 = ns + nd, S2 = ns - nd;
   o[0] = from_fix(S1 + n10, E);

@@ -731,10 +731,13 @@ __global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__re
     const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
     if (bi < c.nb) {
       const long n = c.bnode[bi];
-      double f[8], o[8], dxn, dyn;
+      double f[8], o[8], dxn = 0.0, dyn = 0.0;
       pull_boundary_c(fin, n, g, b, c, bi, f);
-      const Coef cc = node_coef<FIELD>(c0, fl, g.N, n, (int)bi);
-      collide<true>(f, __ldg(g2 + n), __ldg(g2 + g.N + n), cc, o, dxn, dyn);
+      const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+      CoefFix cf;
+      if (ARITH == 0 || !node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf) ||
+          !collide_fix<MONITOR, true>(f, qx, qy, cf, o, dxn, dyn))
+        collide<true>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, (int)bi), o, dxn, dyn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
       if (MONITOR) mon[0] = dxn * dxn + dyn * dyn;
@@ -751,9 +754,12 @@ __global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__re
         for (int k = 0; k < 8; ++k)
           f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
         const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+        // (interior nodes are still all zero in the first sweeps of a traction-driven
+        // solve from rest: they map to zero without the FP64 pipe)
         if (ARITH == 0 ||
             !collide_fix<MONITOR>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
-          collide<false>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, -1), o, dxn, dyn);
+          if (ARITH == 0 || !zero_node(f, qx, qy, o))
+            collide<false>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, -1), o, dxn, dyn);
 #pragma unroll
         for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
         if (MONITOR) mon[0] = dxn * dxn + dyn * dyn;
@@ -780,10 +786,13 @@ __global__ void __launch_bounds__(kCompactThreads) k_adjoint_c(const double *__r
     const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
     if (bi < c.nb) {
       const long n = c.bnode[bi];
-      double p[8], o[8], ax, ay;
+      double p[8], o[8], ax = 0.0, ay = 0.0;
       pull_boundary_adj_c(pin, n, g, b, c, bi, p);
-      const Coef cc = node_coef<FIELD>(c0, fl, g.N, n, (int)bi);
-      collide_T<true>(p, __ldg(r + n), __ldg(r + g.N + n), cc, o, ax, ay);
+      const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
+      CoefFix cf;
+      if (ARITH == 0 || !node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf) ||
+          !collide_T_fix<MONITOR, true>(p, rx, ry, cf, o, ax, ay))
+        collide_T<true>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, (int)bi), o, ax, ay);
 #pragma unroll
       for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
       if (MONITOR) mon[0] = ax * ax + ay * ay;
@@ -802,7 +811,8 @@ __global__ void __launch_bounds__(kCompactThreads) k_adjoint_c(const double *__r
         const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
         if (ARITH == 0 ||
             !collide_T_fix<MONITOR>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
-          collide_T<false>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, -1), o, ax, ay);
+          if (ARITH == 0 || !zero_node(p, rx, ry, o))
+            collide_T<false>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, -1), o, ax, ay);
 #pragma unroll
         for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
         if (MONITOR) mon[0] = ax * ax + ay * ay;
@@ -847,6 +857,30 @@ static __global__ void __launch_bounds__(kCompactThreads) k_residual_c(
   if (threadIdx.x == 0) {
     partial[blockIdx.x * 2 + 0] = v[0];
     partial[blockIdx.x * 2 + 1] = v[1];
+  }
+}
+
+// First adjoint sweep from rest: phi_C(1) = A^T S'^T 0 - j = -j (Eq. adjoint_iteration
+// with phi_C(0) = 0), written without reading the zero state: the values are those of
+// the transposed collision (lbm_device.cuh) with psi = 0, j_k = r . c_k.  Bounded grids
+// write their active nodes only (the others keep the zeros they were created with).
+template <bool BOUNDED>
+__global__ void __launch_bounds__(256) k_adjoint_rest(const double *__restrict__ r,
+                                                      double *__restrict__ pout, Grid g,
+                                                      Bounded b) {
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < g.N;
+       n += (long)gridDim.x * blockDim.x) {
+    if (BOUNDED && b.type[n] == 0) continue;
+    const double rx = r[n], ry = r[g.N + n];
+    const double P1 = -rx - ry, P2 = rx - ry;
+    pout[0 * g.N + n] = -rx;
+    pout[1 * g.N + n] = -ry;
+    pout[2 * g.N + n] = rx;
+    pout[3 * g.N + n] = ry;
+    pout[4 * g.N + n] = P1;
+    pout[5 * g.N + n] = P2;
+    pout[6 * g.N + n] = -P1;
+    pout[7 * g.N + n] = -P2;
   }
 }
 

@@ -42,7 +42,8 @@ struct lbm_solid {
   double alpha = 0.0;  // scalar Young control (E = alpha^2)
   // modulus field control: per-node constants, control copy, per-record gamma / node
   double *qfield = nullptr, *alphaN = nullptr, *gamf = nullptr;
-  FixC *qfix = nullptr;
+  FixC *qfix = nullptr, *bfix = nullptr;
+  uint8_t *bok = nullptr;
   int *bnode = nullptr;
   // compact launch of bounded grids: interior row chunks, boundary rules in compact form
   Compact cmp{};
@@ -76,6 +77,10 @@ struct lbm_solid {
   double *fcur = nullptr, *fnext = nullptr, *pcur = nullptr, *pnext = nullptr;
   bool fcur_is_fs = true;  // fcur holds an explicit f_S; otherwise f_C(t-1)
   bool have_target = false, adjoint_valid = false, adj_warm = false;
+  // r (the adjoint source) is current while r_at == pstate; pstate changes with the
+  // primal state, the force and the target
+  long pstate = 0, r_at = -1;
+  bool pcur_rest = false;  // the adjoint state is phi_C = 0 (not stored)
   double cbar = 0.0;
   long launches = 0;
   std::vector<double> samples;  // monitor samples c of the last criterion-0 solve
@@ -144,6 +149,11 @@ bool material_coefs(double E, double nu, bool bounded, bool neumann, Coef &c, Ma
   c.fx = CoefFix{to_fixc(c.qs), to_fixc(c.qd), to_fixc(c.q11), to_fixc(1.0 / 3.0)};
   c.qs_b = c.cs * (0.25 + 0.5 * c.gam);
   c.P_b = -0.25 * c.gam * c.cs;
+  c.fx.bnd_ok = std::fabs(c.qs_b) < 0.499 && std::fabs(c.P_b) < 0.499;
+  if (c.fx.bnd_ok) {
+    c.fx.qs_b = to_fixc(c.qs_b);
+    c.fx.P_b = to_fixc(c.P_b);
+  }
   // derivatives with respect to E: d omega = -omega^2 d tau
   const double dmu = 1.0 / (2.0 * (1.0 + nu)), dK = 1.0 / (2.0 * (1.0 - nu));
   const double dt11 = dmu / kTh, dts = 2.0 * dK / (1.0 + kTh), dtd = 2.0 * dmu / (1.0 - kTh);
@@ -160,7 +170,7 @@ lbm_status setup_boundary(lbm_solid *h) {
   const unsigned blocks = (unsigned)((h->nb + threads - 1) / threads);
   k_boundary_setup<<<blocks, threads, 0, h->stream>>>(
       h->bnodes, h->nb, h->mat, h->dx, h->Q, h->s, h->dQ, h->ds, h->field ? h->alphaN : nullptr,
-      h->bnode, h->nu, h->gamf, h->R, nullptr);
+      h->bnode, h->nu, h->gamf, h->R, nullptr, h->bfix, h->bok);
   LAUNCHED(h);
   return LBM_OK;
 }
@@ -340,9 +350,20 @@ lbm_status graph_for(lbm_solid *h, int kind, long k, bool mon, cudaGraphExec_t &
 
 // k sweeps (kind 0 primal, 1 adjoint), monitor partials on the last one if mon.
 lbm_status run_sweeps(lbm_solid *h, int kind, long k, bool mon) {
+  if (kind == 0 && k > 0) ++h->pstate;
   if (kind == 0 && h->fcur_is_fs && k > 0) {  // first sweep from an explicit f_S
     lbm_status st = primal_sweep(h, false);
     if (st) return st;
+    --k;
+  }
+  if (kind == 1 && h->pcur_rest && k > 0) {  // first adjoint sweep from rest: -j
+    if (h->periodic)
+      k_adjoint_rest<false><<<148 * 8, 256, 0, h->stream>>>(h->r2, h->pnext, h->grid, h->bnd);
+    else
+      k_adjoint_rest<true><<<148 * 8, 256, 0, h->stream>>>(h->r2, h->pnext, h->grid, h->bnd);
+    LAUNCHED(h);
+    std::swap(h->pcur, h->pnext);
+    h->pcur_rest = false;
     --k;
   }
   while (k > 0) {
@@ -473,6 +494,7 @@ lbm_status check_opts(lbm_solid *h, const lbm_solve_opts *o) {
 }
 
 lbm_status objective_partials(lbm_solid *h) {
+  h->r_at = h->pstate;
   const double scale = h->dx * h->dx / h->cbar;
   if (h->periodic) {
     if (h->fcur_is_fs)
@@ -493,7 +515,7 @@ void free_all(lbm_solid *h) {
   void *bufs[] = {h->fA, h->fB, h->pA, h->pB, h->g2, h->r2, h->dstar, h->obs, h->basis, h->Fbase,
                   h->type, h->regmask, h->bidx, h->Q, h->s, h->dQ, h->ds, h->bnodes,
                   h->partial, h->dres, h->qfield, h->alphaN, h->gamf, h->bnode, h->tA, h->tB,
-                  h->qdot, h->qfix, h->chunk, h->negmask, h->R};
+                  h->qdot, h->qfix, h->chunk, h->negmask, h->R, h->bfix, h->bok};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (h->hres) cudaFreeHost(h->hres);
@@ -659,7 +681,11 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
     ALLOC(h->qfield, 3 * sizeof(double) * N);
     ALLOC(h->qfix, 3 * sizeof(FixC) * N);
     ALLOC(h->alphaN, sizeof(double) * N);
-    if (!h->periodic && h->nb) ALLOC(h->gamf, sizeof(double) * h->nb);
+    if (!h->periodic && h->nb) {
+      ALLOC(h->gamf, sizeof(double) * h->nb);
+      ALLOC(h->bfix, 2 * sizeof(FixC) * h->nb);
+      ALLOC(h->bok, h->nb);
+    }
   }
   if (!h->periodic) {
     ALLOC(h->type, N);
@@ -730,7 +756,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
     std::vector<double> a0(N, std::sqrt(d->E));
     up(h->alphaN, a0.data(), sizeof(double) * N);
     if (e != cudaSuccess) return bail(LBM_ERR_CUDA);
-    h->fl = Field{h->qfield, h->qfix, h->gamf, h->alphaN, h->nu};
+    h->fl = Field{h->qfield, h->qfix, h->gamf, h->bfix, h->bok, h->alphaN, h->nu};
     if (set_field(h) != LBM_OK) return bail(LBM_ERR_CUDA);
   }
   if (h->Fbase) {
@@ -822,6 +848,7 @@ lbm_status lbm_solid_set_control(lbm_solid *h, const double *alpha, size_t n, in
     CK(h, cudaMemsetAsync(h->fcur, 0, sizeof(double) * 8 * h->N, h->stream));
     h->fcur_is_fs = true;
   }
+  ++h->pstate;
   h->adjoint_valid = false;
   h->adj_warm = false;
   return LBM_OK;
@@ -845,6 +872,7 @@ lbm_status lbm_solid_set_target(lbm_solid *h, const double *dstar) {
   if (!(h->hres[0] > 0.0) || !std::isfinite(h->hres[0]))
     return fail(h, LBM_ERR_ARG, "target has zero norm on the observation domain (Cbar = 0)");
   h->cbar = h->hres[0];
+  ++h->pstate;
   h->have_target = true;
   h->adjoint_valid = false;
   return LBM_OK;
@@ -891,9 +919,10 @@ lbm_status lbm_solid_adjoint_solve(lbm_solid *h, const lbm_solve_opts *o, lbm_so
   lbm_status st = check_opts(h, o);
   if (st) return st;
   if (!h->have_target) return fail(h, LBM_ERR_STATE, "adjoint needs set_target first");
-  // constant terms of Algorithm 1: r from the current primal state
-  if ((st = objective_partials(h))) return st;
-  if (!h->adj_warm) CK(h, cudaMemsetAsync(h->pcur, 0, sizeof(double) * 8 * h->N, h->stream));
+  // constant terms of Algorithm 1: r from the current primal state (unless the last
+  // objective already computed it for this state)
+  if (h->r_at != h->pstate && (st = objective_partials(h))) return st;
+  h->pcur_rest = !h->adj_warm;  // from rest: the first sweep writes -j directly
   h->adj_warm = false;
   auto resid = [h](double &v) { return residual(h, h->pcur, h->pnext, v); };
   st = solve_loop(h, o, info, 1, resid);
@@ -1094,12 +1123,14 @@ lbm_status lbm_solid_set_populations(lbm_solid *h, int which, const double *src)
   if (which == 0) {
     CK(h, cudaMemcpyAsync(h->fcur, src, pop, cudaMemcpyDeviceToDevice, h->stream));
     h->fcur_is_fs = true;
+    ++h->pstate;
     h->adjoint_valid = false;
     return LBM_OK;
   }
   if (which == 2) {
     CK(h, cudaMemcpyAsync(h->pcur, src, pop, cudaMemcpyDeviceToDevice, h->stream));
     h->adj_warm = true;
+    h->pcur_rest = false;
     return LBM_OK;
   }
   return fail(h, LBM_ERR_ARG, "which must be 0 (f_S) or 2 (phi_C)");
