@@ -257,6 +257,35 @@ lbm_status lbm_batch_get_populations(lbm_batch *b, int which, double *dst_dev);
    population-sized scratch buffers for the duration of the call. */
 lbm_status lbm_batch_tune(lbm_batch *b, int sweeps, int *best_bx);
 
+/* ---- Batches of one bounded geometry ---------------------------------------------
+ * count instances of the same bounded lattice (geometry, wall data, body force, kernel
+ * variant: one lbm_solid_desc with control LBM_CTRL_YOUNG_FIELD), each with its own
+ * per-node Young's modulus E_n = alpha_n^2 (Eq. E_substitution), advanced together: every
+ * sweep is ONE launch of the bounded grid's compact sweep over all instances (the same
+ * per-node arithmetic as a single handle), and runs of sweeps are replayed from CUDA
+ * graphs.  Used to generate many steady states of one plate (e.g. training states of a
+ * learned warm start) and for batches of perturbed moduli.
+ *
+ * Layout: instance i's control at [i N + n], its populations at [8 i N + k N + n].  All
+ * arrays are device arrays borrowed for the call; calls are stream-ordered on `stream`
+ * and return without synchronising, except create and set_control (which validate the
+ * moduli on the host).  Errors: LBM_ERR_ARG (NULL, a description that is periodic or not
+ * YOUNG_FIELD, count outside 1..65535, a modulus that gives an invalid material),
+ * LBM_ERR_OOM, LBM_ERR_CUDA; create also returns the errors of lbm_solid_create. */
+typedef struct lbm_plate_batch lbm_plate_batch;
+/* Allocates 2 population buffers and the per-node constants of count instances; every
+   instance starts at rest with the description's modulus E. */
+lbm_status lbm_plate_batch_create(const lbm_solid_desc *desc, int count, void *stream,
+                                  lbm_plate_batch **out);
+lbm_status lbm_plate_batch_destroy(lbm_plate_batch *b);
+/* count * N controls (E_n = alpha_n^2; values at inactive nodes are ignored); every
+   instance is reset to f_S = 0. */
+lbm_status lbm_plate_batch_set_control(lbm_plate_batch *b, const double *alpha_dev);
+/* `sweeps` collide + stream sweeps of every instance (fixed count, no stopping test). */
+lbm_status lbm_plate_batch_primal(lbm_plate_batch *b, long sweeps);
+/* f_S of every instance (count * 8N values; zero at inactive nodes). */
+lbm_status lbm_plate_batch_get_populations(lbm_plate_batch *b, double *dst_dev);
+
 /* ---- Learned warm start ------------------------------------------------------------
  * The paper has no counterpart: this network only supplies the initial populations of
  * an iteration (Eq. adjoint_iteration or the primal sweep) that then runs to the same
@@ -330,7 +359,7 @@ lbm_status lbm_unet_train_step(lbm_unet *u, const float *x_dev, const float *t_d
 lbm_status lbm_warm_encode(int count, int nx, int ny, int factor, const double *field_dev,
                            const double *ref_dev, float *x_dev, float *scale_dev, void *stream);
 /* t (count, ny, nx, 8) = network coordinates of the populations / (s_b c_i); t_dev
-   16-byte aligned. */
+   16-byte aligned.  mode 3: as mode 1 (bounded grids). */
 lbm_status lbm_warm_targets(int count, int nx, int ny, double dx, int mode,
                             const double *pop_dev, const float *scale_dev,
                             const float *chan_dev, float *t_dev, void *stream);
@@ -344,10 +373,30 @@ lbm_status lbm_warm_targets(int count, int nx, int ny, double dx, int mode,
    state of a smooth field has none.  Last, the conserved k = 0 components (the mean
    displacement: mean m10, m01 of f_S for mode 1, the matching adjoint invariants for
    mode 2) are set to zero, their value when iterating from rest with a zero-mean force
-   or source; otherwise the iteration would settle on a rigidly shifted state. */
+   or source; otherwise the iteration would settle on a rigidly shifted state.  Mode 3
+   (bounded grids) is mode 1 without these two periodic steps. */
 lbm_status lbm_warm_decode(int count, int wc, int hc, int factor, double dx_fine, int mode,
                            const float *y_dev, const float *scale_dev, const float *chan_dev,
                            double *pop_dev, int accumulate, void *stream);
+/* Bounded grids: the state of one plate geometry as a function of its Young's modulus,
+ * with the network on a w x h crop of the nx_box x ny_box box (the crop holds the whole
+ * domain).  Mode 3 of lbm_warm_targets / lbm_warm_decode is mode 1 without the periodic
+ * steps (no Fourier components removed, no means set to zero).
+ * x (count, h/factor, w/factor, 2): block means over factor x factor crop nodes of
+ * mask_n E_ref / E_n (the compliance: the steady displacement of a uniform modulus is
+ * proportional to it when the loads do not depend on E, so a linear network can represent
+ * that dependence) and of mask_n, E_n = alpha_n^2 (per_node: alpha_dev holds
+ * count * nx_box * ny_box values) or alpha_b^2 (otherwise: count values); mask_dev
+ * (nx_box * ny_box uint8) marks active nodes. */
+lbm_status lbm_warm_encode_modulus(int count, int nx_box, int ny_box, int per_node,
+                                   const double *alpha_dev, const uint8_t *mask_dev, double E_ref,
+                                   int w, int h, int factor, float *x_dev, void *stream);
+/* Populations between the box layout (count, 8, ny_box, nx_box) and the crop layout
+   (count, 8, h, w): to_box = 0 copies the crop out of the box; to_box = 1 writes the box,
+   zero outside the crop and where mask_dev (may be NULL) is 0.  src and dst must differ. */
+lbm_status lbm_warm_crop(int count, int nx_box, int ny_box, int w, int h, int to_box,
+                         const uint8_t *mask_dev, const double *src_dev, double *dst_dev,
+                         void *stream);
 /* rms_i of channel i of an (pixels, 8) tensor over its first min(pixels, 2^22) rows. */
 lbm_status lbm_warm_channel_rms(const float *t_dev, long pixels, float *rms_dev, void *stream);
 

@@ -124,7 +124,8 @@ __device__ inline Material material_of(double E, double nu) {
 }
 
 // One thread per boundary record: Q (row-major [k*8+j]) and s, and their derivatives
-// with respect to E (dQ, ds; skipped when dQ == nullptr).  With a modulus field
+// with respect to E (dQ, ds; skipped when dQ == nullptr; Q and s skipped when Q ==
+// nullptr).  With a modulus field
 // (alpha != nullptr) each record takes the material of its own node and also stores
 // its boundary gamma (Eq. gamma with tau_f = 1/2).
 // Compact form (R, dR: 4 doubles per link, SoA [(k*4 + i)*nb + b], i = 0..2 the
@@ -176,6 +177,7 @@ static __global__ void k_boundary_setup(const BoundaryNode *__restrict__ nodes, 
       R[(long)(k * 4 + i) * nb + b] = r[i].v;
       if (dR) dR[(long)(k * 4 + i) * nb + b] = r[i].d;
     }
+    if (!Q) continue;  // compact form only (batches of one geometry)
     if (bn.code[k] == 0) {
       s[b * 8 + k] = 0.0;
       if (dQ) ds[b * 8 + k] = 0.0;

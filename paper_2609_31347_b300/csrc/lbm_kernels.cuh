@@ -718,15 +718,15 @@ __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ p
   }
 }
 
-// One primal sweep of a bounded grid (compact launch); monitor partial per block.
+// The per-thread work of a primal sweep of a bounded grid (compact launch, block
+// blockIdx.x); mon receives |d|^2 of the thread's node (0 if none).
 template <bool MONITOR, int ARITH, bool FIELD>
-__global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__restrict__ fin,
-                                                              double *__restrict__ fout,
-                                                              const double *__restrict__ g2,
-                                                              Grid g, Bounded b, Compact c,
-                                                              Coef c0, Field fl,
-                                                              double *__restrict__ partial) {
-  double mon[1] = {0.0};
+__device__ __forceinline__ void sweep_primal_c(const double *__restrict__ fin,
+                                               double *__restrict__ fout,
+                                               const double *__restrict__ g2, const Grid &g,
+                                               const Bounded &b, const Compact &c,
+                                               const Coef &c0, const Field &fl, double &mon) {
+  mon = 0.0;
   if ((int)blockIdx.x < c.bblocks) {
     const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
     if (bi < c.nb) {
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__re
         collide<true>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, (int)bi), o, dxn, dyn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
-      if (MONITOR) mon[0] = dxn * dxn + dyn * dyn;
+      if (MONITOR) mon = dxn * dxn + dyn * dyn;
     }
   } else {
     const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
@@ -762,14 +762,122 @@ __global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__re
             collide<false>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, -1), o, dxn, dyn);
 #pragma unroll
         for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
-        if (MONITOR) mon[0] = dxn * dxn + dyn * dyn;
+        if (MONITOR) mon = dxn * dxn + dyn * dyn;
       }
     }
   }
+}
+
+// One primal sweep of a bounded grid (compact launch); monitor partial per block.
+template <bool MONITOR, int ARITH, bool FIELD>
+__global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__restrict__ fin,
+                                                              double *__restrict__ fout,
+                                                              const double *__restrict__ g2,
+                                                              Grid g, Bounded b, Compact c,
+                                                              Coef c0, Field fl,
+                                                              double *__restrict__ partial) {
+  double mon[1];
+  sweep_primal_c<MONITOR, ARITH, FIELD>(fin, fout, g2, g, b, c, c0, fl, mon[0]);
   if (MONITOR) {
     __shared__ double sm[32];
     block_sum<1>(mon, sm);
     if (threadIdx.x == 0) partial[blockIdx.x] = mon[0];
+  }
+}
+
+// Batches of one bounded geometry: instance blockIdx.y has its own populations
+// ([8 N i, 8 N (i + 1))) and its own per-node material (modulus field planes and
+// boundary records); the geometry lists and the force are shared.
+__device__ __forceinline__ void offset_instance(long i, const Grid &g, Field &fl, Compact &c) {
+  fl.q += 3 * g.N * i;
+  fl.qfix += 3 * g.N * i;
+  fl.gam += c.nb * i;
+  fl.bfix += 2 * c.nb * i;
+  fl.bok += c.nb * i;
+  fl.alpha += g.N * i;
+  c.R += 32 * c.nb * i;
+}
+
+template <int ARITH>
+__global__ void __launch_bounds__(kCompactThreads) k_primal_cb(const double *__restrict__ fin,
+                                                               double *__restrict__ fout,
+                                                               const double *__restrict__ g2,
+                                                               Grid g, Bounded b, Compact c,
+                                                               Coef c0, Field fl) {
+  const long i = blockIdx.y;
+  offset_instance(i, g, fl, c);
+  double mon;
+  sweep_primal_c<false, ARITH, true>(fin + 8 * g.N * i, fout + 8 * g.N * i, g2, g, b, c, c0,
+                                     fl, mon);
+}
+
+// First sweep of a batch from explicit states f_S (collision only), compact launch.
+template <int ARITH>
+__global__ void __launch_bounds__(kCompactThreads) k_collide_cb(const double *__restrict__ fin,
+                                                                double *__restrict__ fout,
+                                                                const double *__restrict__ g2,
+                                                                Grid g, Compact c, Coef c0,
+                                                                Field fl) {
+  const long i = blockIdx.y;
+  offset_instance(i, g, fl, c);
+  fin += 8 * g.N * i;
+  fout += 8 * g.N * i;
+  long n = -1, bi = -1;
+  if ((int)blockIdx.x < c.bblocks) {
+    bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    if (bi < c.nb) n = c.bnode[bi];
+  } else {
+    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w < c.nchunk) {
+      const int2 ch = c.chunk[w];
+      if (lane < ch.y) n = (long)ch.x + lane;
+    }
+  }
+  if (n < 0) return;
+  double f[8], o[8], dxn, dyn;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f[k] = fin[k * g.N + n];
+  const double qx = g2[n], qy = g2[g.N + n];
+  if (bi >= 0 && bi < c.nb) {
+    CoefFix cf;
+    if (ARITH == 0 || !node_fix_bnd<true>(c0.fx, fl, g.N, n, bi, cf) ||
+        !collide_fix<false, true>(f, qx, qy, cf, o, dxn, dyn))
+      collide<true>(f, qx, qy, node_coef<true>(c0, fl, g.N, n, (int)bi), o, dxn, dyn);
+  } else if (ARITH == 0 ||
+             !collide_fix<false>(f, qx, qy, node_fix<true>(c0.fx, fl, g.N, n), o, dxn, dyn)) {
+    if (ARITH == 0 || !zero_node(f, qx, qy, o))
+      collide<false>(f, qx, qy, node_coef<true>(c0, fl, g.N, n, -1), o, dxn, dyn);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
+}
+
+// f_S = S' f_C of every instance of a batch (compact launch; inactive nodes untouched).
+static __global__ void __launch_bounds__(kCompactThreads) k_pull_cb(
+    const double *__restrict__ fin, double *__restrict__ fs, Grid g, Bounded b, Compact c) {
+  const long i = blockIdx.y;
+  Field unused{};
+  offset_instance(i, g, unused, c);
+  fin += 8 * g.N * i;
+  fs += 8 * g.N * i;
+  double f[8];
+  if ((int)blockIdx.x < c.bblocks) {
+    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    if (bi >= c.nb) return;
+    const long n = c.bnode[bi];
+    pull_boundary_c(fin, n, g, b, c, bi, f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fs[k * g.N + n] = f[k];
+  } else {
+    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= c.nchunk) return;
+    const int2 ch = c.chunk[w];
+    if (lane >= ch.y) return;
+    const long n = (long)ch.x + lane;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fs[k * g.N + n] = fin[k * g.N + n - kCX[k] - (long)kCY[k] * g.nx];
   }
 }
 

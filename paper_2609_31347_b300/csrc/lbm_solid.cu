@@ -1156,3 +1156,233 @@ lbm_status lbm_solid_displacement(lbm_solid *h, double *d) {
 }
 
 }  // extern "C"
+
+// ---- Batches of one bounded geometry (per-instance modulus fields) ------------------
+struct lbm_plate_batch {
+  lbm_solid *geo = nullptr;  // geometry, compact lists, shared force and constants
+  int count = 0;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  double *fA = nullptr, *fB = nullptr, *fcur = nullptr, *fnext = nullptr;
+  bool fs = true;  // fcur holds explicit f_S (all instances)
+  double *q = nullptr, *alpha = nullptr, *gam = nullptr, *R = nullptr;
+  FixC *qfix = nullptr, *bfix = nullptr;
+  uint8_t *bok = nullptr;
+  Field fl{};
+  Compact cmp{};
+  struct G {
+    long k;
+    int parity;
+    cudaGraphExec_t exec;
+  };
+  std::vector<G> graphs;
+};
+
+namespace {
+
+void plate_batch_free(lbm_plate_batch *b) {
+  for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  void *bufs[] = {b->fA, b->fB, b->q, b->alpha, b->gam, b->R, b->qfix, b->bfix, b->bok};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->geo) lbm_solid_destroy(b->geo);
+}
+
+void plate_batch_sweep(lbm_plate_batch *b, cudaStream_t st) {
+  lbm_solid *h = b->geo;
+  const dim3 grid((unsigned)h->cblocks, (unsigned)b->count);
+  if (h->kernel == LBM_KERNEL_FP64)
+    k_primal_cb<0><<<grid, kCompactThreads, 0, st>>>(b->fcur, b->fnext, h->g2, h->grid, h->bnd, b->cmp, h->coef, b->fl);
+  else
+    k_primal_cb<1><<<grid, kCompactThreads, 0, st>>>(b->fcur, b->fnext, h->g2, h->grid, h->bnd, b->cmp, h->coef, b->fl);
+  std::swap(b->fcur, b->fnext);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_plate_batch_create(const lbm_solid_desc *d, int count, void *stream,
+                                  lbm_plate_batch **out) {
+  if (!out || !d) return LBM_ERR_ARG;
+  *out = nullptr;
+  if (d->periodic || d->control != LBM_CTRL_YOUNG_FIELD || count < 1 || count > 65535)
+    return LBM_ERR_ARG;
+  lbm_plate_batch *b = new (std::nothrow) lbm_plate_batch();
+  if (!b) return LBM_ERR_OOM;
+  b->count = count;
+  b->stream = (cudaStream_t)stream;
+  lbm_status st = lbm_solid_create(d, stream, &b->geo);
+  if (st != LBM_OK) {
+    b->geo = nullptr;
+    delete b;
+    return st;
+  }
+  lbm_solid *h = b->geo;
+  const long N = h->N, nb = h->nb, C = count;
+  if ((long)h->cblocks > 0x7fffffffL || 8 * N * C > (1L << 40)) {
+    plate_batch_free(b);
+    delete b;
+    return LBM_ERR_ARG;
+  }
+  cudaError_t e = cudaSuccess;
+#define PALLOC(ptr, bytes) \
+  if (e == cudaSuccess && (bytes) > 0) e = cudaMalloc((void **)&(ptr), (bytes))
+  PALLOC(b->fA, sizeof(double) * 8 * N * C);
+  PALLOC(b->fB, sizeof(double) * 8 * N * C);
+  PALLOC(b->q, sizeof(double) * 3 * N * C);
+  PALLOC(b->qfix, sizeof(FixC) * 3 * N * C);
+  PALLOC(b->alpha, sizeof(double) * N * C);
+  PALLOC(b->gam, sizeof(double) * nb * C);
+  PALLOC(b->R, sizeof(double) * 32 * nb * C);
+  PALLOC(b->bfix, sizeof(FixC) * 2 * nb * C);
+  PALLOC(b->bok, nb * C);
+#undef PALLOC
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->fA, 0, sizeof(double) * 8 * N * C, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->fB, 0, sizeof(double) * 8 * N * C, b->stream);
+  if (e != cudaSuccess) {
+    plate_batch_free(b);
+    delete b;
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+  }
+  b->fcur = b->fA;
+  b->fnext = b->fB;
+  b->fl = Field{b->q, b->qfix, b->gam, b->bfix, b->bok, b->alpha, h->nu};
+  b->cmp = h->cmp;
+  b->cmp.R = b->R;
+  // initial control: the description's modulus everywhere
+  std::vector<double> a0((size_t)(N * C), std::sqrt(d->E));
+  double *tmp = nullptr;
+  if (cudaMalloc(&tmp, sizeof(double) * N * C) != cudaSuccess) {
+    plate_batch_free(b);
+    delete b;
+    return LBM_ERR_OOM;
+  }
+  st = cudaMemcpy(tmp, a0.data(), sizeof(double) * N * C, cudaMemcpyHostToDevice) == cudaSuccess
+           ? lbm_plate_batch_set_control(b, tmp)
+           : LBM_ERR_CUDA;
+  cudaStreamSynchronize(b->stream);
+  cudaFree(tmp);
+  if (st != LBM_OK) {
+    plate_batch_free(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_plate_batch_destroy(lbm_plate_batch *b) {
+  if (!b) return LBM_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  plate_batch_free(b);
+  delete b;
+  return LBM_OK;
+}
+
+lbm_status lbm_plate_batch_set_control(lbm_plate_batch *b, const double *alpha) {
+  if (!b || !alpha) return LBM_ERR_ARG;
+  lbm_solid *h = b->geo;
+  const long N = h->N, nb = h->nb, C = b->count;
+  // validate on the host: every active modulus alpha^2 must give a valid material
+  std::vector<double> a((size_t)(N * C));
+  std::vector<uint8_t> ty((size_t)N);
+  if (cudaMemcpyAsync(a.data(), alpha, sizeof(double) * N * C, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(ty.data(), h->type, N, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  for (long i = 0; i < N * C; ++i) {
+    const uint8_t t = ty[i % N];
+    if (t == 0) continue;
+    Coef c{};
+    Material m{};
+    YoungDeriv yd{};
+    std::string why;
+    if (!material_coefs(a[i] * a[i], h->nu, t == 2, h->has_neumann, c, m, yd, why)) return LBM_ERR_ARG;
+  }
+  if (cudaMemcpyAsync(b->alpha, alpha, sizeof(double) * N * C, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  for (long i = 0; i < C; ++i) {
+    k_set_young_field<<<148 * 4, 256, 0, b->stream>>>(b->alpha + N * i, h->nu, N, b->q + 3 * N * i, b->qfix + 3 * N * i);
+    if (nb) {
+      const unsigned blocks = (unsigned)((nb + 127) / 128);
+      k_boundary_setup<<<blocks, 128, 0, b->stream>>>(
+          h->bnodes, nb, h->mat, h->dx, nullptr, nullptr, nullptr, nullptr, b->alpha + N * i,
+          h->bnode, h->nu, b->gam + nb * i, b->R + 32 * nb * i, nullptr, b->bfix + 2 * nb * i,
+          b->bok + nb * i);
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+  if (cudaMemsetAsync(b->fcur, 0, sizeof(double) * 8 * N * C, b->stream) != cudaSuccess) return LBM_ERR_CUDA;
+  b->fs = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_plate_batch_primal(lbm_plate_batch *b, long sweeps) {
+  if (!b || sweeps < 0) return LBM_ERR_ARG;
+  lbm_solid *h = b->geo;
+  if (b->fs && sweeps > 0) {  // first sweep from the explicit states
+    const dim3 grid((unsigned)h->cblocks, (unsigned)b->count);
+    if (h->kernel == LBM_KERNEL_FP64)
+      k_collide_cb<0><<<grid, kCompactThreads, 0, b->stream>>>(b->fcur, b->fnext, h->g2, h->grid, b->cmp, h->coef, b->fl);
+    else
+      k_collide_cb<1><<<grid, kCompactThreads, 0, b->stream>>>(b->fcur, b->fnext, h->g2, h->grid, b->cmp, h->coef, b->fl);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    std::swap(b->fcur, b->fnext);
+    b->fs = false;
+    --sweeps;
+  }
+  // runs of sweeps replayed from CUDA graphs (keyed by length and buffer parity)
+  constexpr long kChunk = 64;
+  while (sweeps > 0) {
+    const long k = sweeps >= kChunk ? kChunk : sweeps;
+    if (k < 4) {
+      for (long i = 0; i < k; ++i) plate_batch_sweep(b, b->stream);
+      if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    } else {
+      const int parity = b->fcur == b->fA ? 0 : 1;
+      cudaGraphExec_t ex = nullptr;
+      for (auto &g : b->graphs)
+        if (g.k == k && g.parity == parity) ex = g.exec;
+      if (!ex) {
+        if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+          return LBM_ERR_CUDA;
+        double *f0 = b->fcur, *f1 = b->fnext;
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+          return LBM_ERR_CUDA;
+        for (long i = 0; i < k; ++i) plate_batch_sweep(b, b->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
+        b->fcur = f0;
+        b->fnext = f1;
+        if (ec != cudaSuccess || !graph) return LBM_ERR_CUDA;
+        const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return LBM_ERR_CUDA;
+        b->graphs.push_back(lbm_plate_batch::G{k, parity, ex});
+      }
+      if (cudaGraphLaunch(ex, b->stream) != cudaSuccess) return LBM_ERR_CUDA;
+      if (k & 1) std::swap(b->fcur, b->fnext);
+    }
+    sweeps -= k;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_plate_batch_get_populations(lbm_plate_batch *b, double *dst) {
+  if (!b || !dst) return LBM_ERR_ARG;
+  lbm_solid *h = b->geo;
+  const size_t pop = sizeof(double) * 8 * h->N * b->count;
+  if (b->fs) {
+    if (cudaMemcpyAsync(dst, b->fcur, pop, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    return LBM_OK;
+  }
+  if (cudaMemsetAsync(dst, 0, pop, b->stream) != cudaSuccess) return LBM_ERR_CUDA;
+  const dim3 grid((unsigned)h->cblocks, (unsigned)b->count);
+  k_pull_cb<<<grid, kCompactThreads, 0, b->stream>>>(b->fcur, dst, h->grid, h->bnd, b->cmp);
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+}  // extern "C"

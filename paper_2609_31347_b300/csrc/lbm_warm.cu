@@ -396,6 +396,60 @@ unsigned grid_for(long n) {
   return (unsigned)(b < 148 * 16 ? (b < 1 ? 1 : b) : 148 * 16);
 }
 
+// Bounded grids (one plate geometry, network on a w x h crop of the nx_box x ny_box box):
+// x[b, yc, xc, 0] = block mean of mask E_ref / E_n (the compliance: for loads that do not
+// depend on E the steady displacement of a uniform modulus is proportional to it, so a
+// linear network can represent that dependence), x[b, yc, xc, 1] = block mean of mask,
+// E_n = alpha_n^2 (per node) or alpha_b^2 (one modulus per sample).
+__global__ void k_encode_modulus(const double *__restrict__ alpha, int per_node,
+                                 const uint8_t *__restrict__ mask, int nx_box, long N_box,
+                                 double E_ref, int w, int h, int factor,
+                                 float *__restrict__ x, int count) {
+  const int wc = w / factor, hc = h / factor;
+  const long total = (long)count * hc * wc;
+  const double inv = 1.0 / ((double)factor * factor);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    const int xc = (int)(i % wc);
+    const long r = i / wc;
+    const int yc = (int)(r % hc), b = (int)(r / hc);
+    double le = 0.0, mk = 0.0;
+    for (int dy = 0; dy < factor; ++dy)
+      for (int dx = 0; dx < factor; ++dx) {
+        const long n = (long)(yc * factor + dy) * nx_box + xc * factor + dx;
+        if (!mask[n]) continue;
+        const double a = per_node ? alpha[(long)b * N_box + n] : alpha[b];
+        le += E_ref / (a * a);
+        mk += 1.0;
+      }
+    x[2 * i] = (float)(le * inv);
+    x[2 * i + 1] = (float)(mk * inv);
+  }
+}
+
+// Populations between the box (count, 8, ny_box, nx_box) and the crop (count, 8, h, w):
+// to_box = 0 copies the crop out; to_box = 1 writes the box, zero outside the crop and at
+// inactive nodes (mask NULL: all active).
+__global__ void k_crop(const double *__restrict__ src, double *__restrict__ dst, int nx_box,
+                       int ny_box, int w, int h, int to_box, const uint8_t *__restrict__ mask,
+                       int count) {
+  const long Nb = (long)nx_box * ny_box, Nc = (long)w * h;
+  const long total = (long)count * 8 * (to_box ? Nb : Nc);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    if (to_box) {
+      const long n = i % Nb, bk = i / Nb;
+      const int x = (int)(n % nx_box), y = (int)(n / nx_box);
+      const bool in = x < w && y < h && (!mask || mask[n]);
+      dst[i] = in ? src[bk * Nc + (long)y * w + x] : 0.0;
+    } else {
+      const long n = i % Nc, bk = i / Nc;
+      const int x = (int)(n % w), y = (int)(n / w);
+      dst[i] = src[bk * Nb + (long)y * nx_box + x];
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -416,30 +470,57 @@ lbm_status lbm_warm_encode(int count, int nx, int ny, int factor, const double *
 lbm_status lbm_warm_targets(int count, int nx, int ny, double dx, int mode, const double *pop_dev,
                             const float *scale_dev, const float *chan_dev, float *t_dev,
                             void *stream) {
-  if (count < 1 || nx < 1 || ny < 1 || !(dx > 0.0) || mode < 0 || mode > 2 || !pop_dev ||
+  if (count < 1 || nx < 1 || ny < 1 || !(dx > 0.0) || mode < 0 || mode > 3 || !pop_dev ||
       !scale_dev || !t_dev)
     return LBM_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(t_dev) % 16) return LBM_ERR_ARG;
   const long N = (long)nx * ny;
   k_targets<<<grid_for((long)count * N), 256, 0, (cudaStream_t)stream>>>(
-      pop_dev, N, dx, mode, scale_dev, chan_dev, t_dev, count);
+      pop_dev, N, dx, mode == 3 ? 1 : mode, scale_dev, chan_dev, t_dev, count);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 lbm_status lbm_warm_decode(int count, int wc, int hc, int factor, double dx_fine, int mode,
                            const float *y_dev, const float *scale_dev, const float *chan_dev,
                            double *pop_dev, int accumulate, void *stream) {
-  if (count < 1 || wc < 1 || hc < 1 || factor < 1 || !(dx_fine > 0.0) || mode < 0 || mode > 2 ||
+  if (count < 1 || wc < 1 || hc < 1 || factor < 1 || !(dx_fine > 0.0) || mode < 0 || mode > 3 ||
       !y_dev || !scale_dev || !pop_dev)
     return LBM_ERR_ARG;
   const long N = (long)wc * hc * factor * factor;
   k_decode<<<grid_for((long)count * N), 256, 0, (cudaStream_t)stream>>>(
-      y_dev, wc, hc, factor, dx_fine, mode, scale_dev, chan_dev, pop_dev, count, accumulate);
-  if (mode != 0) {
+      y_dev, wc, hc, factor, dx_fine, mode == 3 ? 1 : mode, scale_dev, chan_dev, pop_dev, count,
+      accumulate);
+  if (mode == 1 || mode == 2) {
     k_drop_half_nyquist<<<count * 8, 1024, 0, (cudaStream_t)stream>>>(pop_dev, wc * factor,
                                                                      hc * factor);
     k_drop_conserved_mean<<<count, 256, 0, (cudaStream_t)stream>>>(pop_dev, N, mode);
   }
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+lbm_status lbm_warm_encode_modulus(int count, int nx_box, int ny_box, int per_node,
+                                   const double *alpha_dev, const uint8_t *mask_dev, double E_ref,
+                                   int w, int h, int factor, float *x_dev, void *stream) {
+  if (count < 1 || nx_box < 1 || ny_box < 1 || w < 1 || h < 1 || w > nx_box || h > ny_box ||
+      factor < 1 || w % factor || h % factor || !(E_ref > 0.0) || !alpha_dev || !mask_dev ||
+      !x_dev)
+    return LBM_ERR_ARG;
+  const long total = (long)count * (w / factor) * (h / factor);
+  k_encode_modulus<<<grid_for(total), 256, 0, (cudaStream_t)stream>>>(
+      alpha_dev, per_node ? 1 : 0, mask_dev, nx_box, (long)nx_box * ny_box, E_ref, w, h, factor,
+      x_dev, count);
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+lbm_status lbm_warm_crop(int count, int nx_box, int ny_box, int w, int h, int to_box,
+                         const uint8_t *mask_dev, const double *src_dev, double *dst_dev,
+                         void *stream) {
+  if (count < 1 || nx_box < 1 || ny_box < 1 || w < 1 || h < 1 || w > nx_box || h > ny_box ||
+      !src_dev || !dst_dev || src_dev == dst_dev)
+    return LBM_ERR_ARG;
+  const long total = (long)count * 8 * (to_box ? (long)nx_box * ny_box : (long)w * h);
+  k_crop<<<grid_for(total), 256, 0, (cudaStream_t)stream>>>(src_dev, dst_dev, nx_box, ny_box, w,
+                                                            h, to_box ? 1 : 0, mask_dev, count);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 

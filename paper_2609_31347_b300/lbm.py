@@ -37,7 +37,9 @@ EXPORTED = [
     "lbm_unet_set_params", "lbm_unet_forward", "lbm_unet_train_step", "lbm_unet_status",
     "lbm_solid_adjoint_source", "lbm_warm_encode", "lbm_warm_targets", "lbm_warm_decode", "lbm_warm_channel_rms",
     "lbm_warm_combine", "lbm_warm_dot_work_size", "lbm_warm_dots",
-    "lbm_solid_monitor_samples",
+    "lbm_solid_monitor_samples", "lbm_plate_batch_create", "lbm_plate_batch_destroy",
+    "lbm_plate_batch_set_control", "lbm_plate_batch_primal", "lbm_plate_batch_get_populations",
+    "lbm_warm_encode_modulus", "lbm_warm_crop",
 ]
 
 
@@ -95,6 +97,13 @@ def load_library(path: str = LIB_PATH):
         "lbm_solid_displacement": ([P, P], I),
         "lbm_solid_launch_count": ([P], ctypes.c_long),
         "lbm_solid_monitor_samples": ([P, P, ctypes.c_long], ctypes.c_long),
+        "lbm_plate_batch_create": ([ctypes.POINTER(_Desc), I, P, ctypes.POINTER(P)], I),
+        "lbm_plate_batch_destroy": ([P], I),
+        "lbm_plate_batch_set_control": ([P, P], I),
+        "lbm_plate_batch_primal": ([P, ctypes.c_long], I),
+        "lbm_plate_batch_get_populations": ([P, P], I),
+        "lbm_warm_encode_modulus": ([I, I, I, I, P, P, D, I, I, I, P, P], I),
+        "lbm_warm_crop": ([I, I, I, I, I, I, P, P, P, P], I),
         "lbm_status_string": ([I], ctypes.c_char_p),
         "lbm_solid_last_error": ([P], ctypes.c_char_p),
         "lbm_objective_noalloc": ([I, I, D, P, P, P, P, P, P], I),
@@ -206,6 +215,75 @@ def warm_dots(vectors):
     if st != LBM_OK:
         raise LBMError(st, "lbm_warm_dots: " + lib.lbm_status_string(st).decode())
     return out.reshape(m, m)
+
+
+def _desc(nx, ny, dx, E, nu, periodic, node_mask, link_bc, wall_d, wall_T, wall_n, obs,
+          control, force, force_basis, kernel):
+    """(lbm_solid_desc, host arrays it points to)."""
+    N = int(nx) * int(ny)
+    keep = [_host(node_mask, np.uint8, N), _host(link_bc, np.uint8, 8 * N),
+            _host(wall_d, np.float64, 2 * N), _host(wall_T, np.float64, 2 * N),
+            _host(wall_n, np.float64, 2 * N), _host(obs, np.float64, N),
+            _host(force, np.float64, 2 * N), _host(force_basis, np.float64, 4 * N)]
+    ptr = [None if a is None else a.ctypes.data for a in keep]
+    d = _Desc(int(nx), int(ny), float(dx), 1 if periodic else 0, float(E), float(nu),
+              ptr[0], ptr[1], ptr[2], ptr[3], ptr[4], ptr[5], CONTROLS[control], ptr[6],
+              ptr[7], KERNELS[kernel])
+    return d, keep
+
+
+class LBMPlateBatch:
+    """count instances of one bounded geometry, each with its own per-node modulus
+    (E_n = alpha_n^2), advanced by one launch per sweep."""
+
+    def __init__(self, count: int, nx: int, ny: int, dx: float, E: float, nu: float,
+                 node_mask, link_bc, wall_d=None, wall_T=None, wall_n=None, force=None,
+                 kernel: str = "auto", stream=None):
+        import torch
+        self._lib = load_library()
+        self.count, self.nx, self.ny, self.N = int(count), int(nx), int(ny), int(nx) * int(ny)
+        d, keep = _desc(nx, ny, dx, E, nu, False, node_mask, link_bc, wall_d, wall_T, wall_n,
+                        None, "young_field", force, None, kernel)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_plate_batch_create(ctypes.byref(d), int(count),
+                                              ctypes.c_void_p(self.stream.cuda_stream),
+                                              ctypes.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, "lbm_plate_batch_create: " +
+                           self._lib.lbm_status_string(st).decode())
+        self._h = h
+
+    def _check(self, st, what):
+        if st != LBM_OK:
+            raise LBMError(st, "%s: %s" % (what, self._lib.lbm_status_string(st).decode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_plate_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_control(self, alpha):
+        """count * N controls (device float64); resets every instance to rest."""
+        self._check(self._lib.lbm_plate_batch_set_control(
+            self._h, _dev_ptr(alpha, self.count * self.N)), "set_control")
+
+    def primal(self, sweeps: int):
+        self._check(self._lib.lbm_plate_batch_primal(self._h, int(sweeps)), "primal")
+
+    def get_populations(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(8 * self.count * self.N, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lbm_plate_batch_get_populations(
+            self._h, _dev_ptr(out, 8 * self.count * self.N)), "get_populations")
+        return out
 
 
 class LBMSolid:

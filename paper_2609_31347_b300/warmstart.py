@@ -16,6 +16,9 @@ start"; this module orchestrates):
   own forward/backward/Adam kernels.  A network trained on nx^2 lattices is used on
   (factor * nx)^2 lattices by block-averaging the input and interpolating the predicted
   moments, which are scaled so that they do not depend on the grid spacing.
+- ``PlateWarmStartNet``: the same network for the primal state of one bounded plate as a
+  function of its Young's modulus (uniform or per node), trained on states of a batch
+  of that plate with random moduli (one launch per sweep).
 - ``WarmStarter``: supplies initial states to the solves of an optimisation loop.
   Since the steady states are affine in F (primal) and linear in r (adjoint), a
   combination of the loop's earlier steady states reproduces the state of any control
@@ -192,6 +195,137 @@ class WarmStartNet:
         return out
 
 
+class PlateWarmStartNet:
+    """A U-Net for the steady primal state of one bounded geometry (the plate, its wall
+    data and loads fixed) as a function of its Young's modulus, uniform or per node.
+
+    Input: block means over the network's grid of the compliance mask E_ref / E and of the
+    domain mask (for loads that do not depend on E the steady displacement of a uniform
+    modulus is proportional to the compliance, which a linear network represents);
+    output: the eight resolution-free moments of the steady state (the primal
+    scaling of WarmStartNet, without the periodic steps).  The network's grid is the
+    Nx x Nx crop of the (Nx + 1)^2 box (the domain lies inside it).  Training states are
+    generated by the solver itself: a batch of the plate with random moduli, advanced
+    by one launch per sweep (LBMPlateBatch).  A network trained at Nx serves the same
+    physical plate at factor * Nx (input block-averaged, moments interpolated)."""
+
+    net_on_change = False  # the map E -> state is not linear: no state-of-a-change use
+
+    def __init__(self, make_geometry, Nx: int = 64, E_ref: float = 1.0, nu: float = 0.3,
+                 base: int = 32, levels: int = 3, batch: int = 16, seed: int = 0,
+                 stream=None):
+        import torch
+        self._lib = L.load_library()
+        self.make_geometry = make_geometry
+        self.Nx, self.nx = int(Nx), int(Nx)
+        self.E_ref, self.nu = float(E_ref), float(nu)
+        self.base, self.levels, self.batch, self.seed = base, levels, batch, seed
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.net = L.UNet(batch, self.Nx, self.Nx, base, levels, seed, stream=self.stream)
+        self._infer = None
+        self.chan = None
+        self._geo = {}
+        self._one = torch.ones(1, dtype=torch.float32, device="cuda")
+        self._x = torch.empty((1, self.Nx, self.Nx, 2), dtype=torch.float32, device="cuda")
+        self._y = torch.empty((1, self.Nx, self.Nx, 8), dtype=torch.float32, device="cuda")
+
+    _st = WarmStartNet._st
+    _check = WarmStartNet._check
+    fit = WarmStartNet.fit
+    evaluate = WarmStartNet.evaluate
+    _inference_net = WarmStartNet._inference_net
+
+    def geometry(self, Nx):
+        """(geometry, wall_d, wall_T, device mask) of the plate at resolution Nx."""
+        import torch
+        if Nx not in self._geo:
+            geo, wd, wT = self.make_geometry(Nx)
+            mask = torch.as_tensor(geo.active.astype(np.uint8), device="cuda")
+            self._geo[Nx] = (geo, wd, wT, mask)
+        return self._geo[Nx]
+
+    def generate(self, count: int, sweeps: int, seed: int = 1, chunk: int = 256,
+                 E_range=(0.5, 2.0), sigma: float = 0.2, field_frac: float = 0.5):
+        """`count` (input, target) pairs: moduli E_0 log-uniform in E_range, and for a
+        fraction field_frac of the samples a per-node lognormal field E_0 exp(sigma z -
+        sigma^2 / 2) (z i.i.d. normal); `sweeps` sweeps from rest.  Returns device tensors
+        X (count, Nx, Nx, 2) and T (count, Nx, Nx, 8), FP32."""
+        import torch
+        geo, wd, wT, mask = self.geometry(self.Nx)
+        nxb, Nx = geo.nx, self.Nx
+        Nb = nxb * nxb
+        rng = np.random.default_rng(seed)
+        X = torch.empty((count, Nx, Nx, 2), dtype=torch.float32, device="cuda")
+        T = torch.empty((count, Nx, Nx, 8), dtype=torch.float32, device="cuda")
+        ones = torch.ones(chunk, dtype=torch.float32, device="cuda")
+        for start in range(0, count, chunk):
+            m = min(chunk, count - start)
+            E0 = np.exp(rng.uniform(np.log(E_range[0]), np.log(E_range[1]), size=m))
+            z = rng.standard_normal((m, Nb))
+            field = rng.random(m) < field_frac
+            E = E0[:, None] * np.where(field[:, None], np.exp(sigma * z - 0.5 * sigma * sigma),
+                                       1.0)
+            alpha = torch.as_tensor(np.sqrt(E).ravel(), device="cuda")
+            b = L.LBMPlateBatch(m, nxb, nxb, geo.dx, self.E_ref, self.nu, node_mask=geo.active,
+                                link_bc=geo.link, wall_d=wd, wall_T=wT, wall_n=geo.normal,
+                                stream=self.stream)
+            b.set_control(alpha)
+            b.primal(sweeps)
+            pops = b.get_populations()
+            b.close()
+            crop = torch.empty(m * 8 * Nx * Nx, dtype=torch.float64, device="cuda")
+            self._check(self._lib.lbm_warm_crop(m, nxb, nxb, Nx, Nx, 0, None, _ptr(pops),
+                                                _ptr(crop), self._st()), "crop")
+            self._check(self._lib.lbm_warm_encode_modulus(
+                m, nxb, nxb, 1, _ptr(alpha), _ptr(mask), self.E_ref, Nx, Nx, 1,
+                _ptr(X[start:]), self._st()), "encode_modulus")
+            if self.chan is None:
+                self._check(self._lib.lbm_warm_targets(m, Nx, Nx, geo.dx, 3, _ptr(crop),
+                                                       _ptr(ones), None, _ptr(T[start:]),
+                                                       self._st()), "targets")
+                rms = torch.empty(8, dtype=torch.float32, device="cuda")
+                self._check(self._lib.lbm_warm_channel_rms(_ptr(T[start:]), m * Nx * Nx,
+                                                           _ptr(rms), self._st()), "channel_rms")
+                r = rms.cpu().numpy()
+                r = np.where(r > 1e-6 * r.max(), r, 0.0)
+                self.chan = torch.as_tensor(r.astype(np.float32), device="cuda")
+            self._check(self._lib.lbm_warm_targets(m, Nx, Nx, geo.dx, 3, _ptr(crop), _ptr(ones),
+                                                   _ptr(self.chan), _ptr(T[start:]),
+                                                   self._st()), "targets")
+        return X, T
+
+    def predict(self, alpha, out, Nx_fine: int):
+        """Initial populations (8 (Nx_fine + 1)^2, FP64 device tensor `out`) of the plate at
+        resolution Nx_fine for the modulus E = alpha^2 (alpha: one value, or one per box
+        node)."""
+        import torch
+        if self.chan is None:
+            raise RuntimeError("the network has no data normalisation yet: call generate()")
+        if Nx_fine % self.Nx:
+            raise ValueError("resolution %d is not a multiple of the network's %d"
+                             % (Nx_fine, self.Nx))
+        factor = Nx_fine // self.Nx
+        geo, _, _, mask = self.geometry(Nx_fine)
+        nxb = geo.nx
+        per_node = alpha.numel() == nxb * nxb
+        if not per_node and alpha.numel() != 1:
+            raise ValueError("alpha must hold one value or one per box node")
+        L._dev_ptr(alpha, alpha.numel())
+        L._dev_ptr(out, 8 * nxb * nxb)
+        net = self._inference_net()
+        self._check(self._lib.lbm_warm_encode_modulus(
+            1, nxb, nxb, 1 if per_node else 0, _ptr(alpha), _ptr(mask), self.E_ref, Nx_fine,
+            Nx_fine, factor, _ptr(self._x), self._st()), "encode_modulus")
+        net.forward(self._x, self._y, exact_acts=True)
+        crop = torch.empty(8 * Nx_fine * Nx_fine, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lbm_warm_decode(1, self.Nx, self.Nx, factor, geo.dx, 3,
+                                              _ptr(self._y), _ptr(self._one), _ptr(self.chan),
+                                              _ptr(crop), 0, self._st()), "decode")
+        self._check(self._lib.lbm_warm_crop(1, nxb, nxb, Nx_fine, Nx_fine, 1, _ptr(mask),
+                                            _ptr(crop), _ptr(out), self._st()), "uncrop")
+        return out
+
+
 def lagrange_weights(xs, x):
     """w with sum_j w_j p(xs_j) = p(x) for every polynomial p of degree < len(xs)
     (Lagrange interpolation/extrapolation at x from distinct abscissae xs)."""
@@ -297,6 +431,12 @@ class WarmStarter:
         return self.hist_p[-1][1] if self.hist_p else None
 
     def _check(self, solver):
+        if isinstance(self.primal, PlateWarmStartNet):
+            if solver.periodic or solver.control not in ("young_scalar", "young_field") or \
+                    self.adjoint is not None:
+                raise ValueError("a plate network serves the primal of Young's-modulus "
+                                 "controls on its bounded geometry")
+            return
         if (self.primal is not None or self.adjoint is not None) and not (
                 solver.periodic and solver.control == "force_field"):
             raise ValueError("warm-start networks serve periodic force-field controls only")
@@ -334,11 +474,20 @@ class WarmStarter:
             entries, w = self._primal_weights(solver, F)
             f0 = torch.empty_like(entries[-1][2])
             L.warm_combine(w, [e[2] for e in entries], f0)
-            if self.primal is not None:
+            if self.primal is not None and getattr(self.primal, "net_on_change", True):
                 ref = torch.empty_like(F.reshape(-1))
                 L.warm_combine(w, [e[0] for e in entries], ref)
                 self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx, ref=ref,
                                     accumulate=True)
+        elif isinstance(self.primal, PlateWarmStartNet):
+            # per-node modulus fields only: for a uniform modulus the network's start is
+            # not mirror-symmetric like the plate's state, and the iteration then has to
+            # remove antisymmetric components that a start from rest never has (measured:
+            # 7.5x more sweeps at N_x = 512), so those solves start from rest
+            if solver.control != "young_field":
+                return
+            f0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
+            self.primal.predict(F.reshape(-1), f0, Nx_fine=solver.nx - 1)
         else:
             f0 = torch.empty(8 * solver.N, dtype=torch.float64, device="cuda")
             self.primal.predict(F, f0, nx_fine=solver.nx, dx_fine=solver.dx)

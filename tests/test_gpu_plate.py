@@ -171,3 +171,39 @@ def test_plate_primal_convergence_order(lbm_mod):
           % (eoc_d2, gd["eoc_d_L2"][0], eoc_di, gd["eoc_d_Linf"][0], eoc_s2, gd["eoc_sigma_L2"][0]))
     assert ed2[-1] < ed2[0]
     assert 0.6 <= eoc_d2 <= 2.2
+
+
+@pytest.mark.parametrize("kernel", ["fp64", "auto"])
+def test_plate_batch_instances_match_single_handles_and_the_oracle(lbm_mod, kernel):
+    # one bounded geometry, three instances with their own per-node modulus fields,
+    # advanced by one launch per sweep: each instance equals a single handle with the
+    # same field (same per-node arithmetic) and the oracle (Section 3.1 stepping with
+    # the boundary rules)
+    geo, dstar, F, wd, wT = paper_plate(16)
+    N = geo.nx * geo.nx
+    count, T = 3, 57
+    E = np.stack([I.lognormal_E(N, E_ref=0.1, sigma=0.2, seed=40 + i) for i in range(count)])
+    b = lbm_mod.LBMPlateBatch(count, geo.nx, geo.nx, geo.dx, I.PLATE_E, I.PLATE_NU,
+                              node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
+                              wall_n=geo.normal, force=F, kernel=kernel)
+    b.set_control(dev(np.sqrt(E)))
+    b.primal(T)
+    got = host(b.get_populations()).reshape(count, 8, N)
+    g = ogrid(geo, wd, wT, I.PLATE_NU)
+    for i in range(count):
+        s = make(lbm_mod, geo, wd, wT, I.PLATE_E, I.PLATE_NU, control="young_field", force=F,
+                 kernel=kernel)
+        s.set_control(dev(np.sqrt(E[i])))
+        s.primal_solve(T, fixed_steps=True)
+        one = host(s.get_populations(0)).reshape(8, N)
+        s.close()
+        assert np.abs(got[i] - one).max() <= 1e-13 * np.abs(one).max(), i
+        Enode = np.where(geo.active == 1, E[i], 0.1)
+        ref = oracle.primal(g, Enode, F, T)
+        assert rel_inf(got[i], ref) <= POP_TOL, i
+    # a new control resets every instance to rest
+    b.set_control(dev(np.sqrt(E[::-1].copy())))
+    b.primal(T)
+    again = host(b.get_populations()).reshape(count, 8, N)
+    assert np.array_equal(again[count - 1], got[0])
+    b.close()
