@@ -115,8 +115,23 @@ def test_targets_are_the_scaled_moments_and_decode_inverts_them(lbm):
                                 ptr(t), stream()) == 0
     tt = t.cpu().numpy()
     assert np.all(tt[..., 5:7] == 0) and np.all(np.isfinite(tt))
+    # mode 3 (bounded grids): the targets of mode 1, decoded without the periodic steps
+    t1 = torch.empty_like(t)
+    assert lib.lbm_warm_targets(count, nx, nx, dx, 1, ptr(dev(pops)), ptr(s), None,
+                                ptr(t1), stream()) == 0
     assert lib.lbm_warm_targets(count, nx, nx, dx, 3, ptr(dev(pops)), ptr(s), None,
+                                ptr(t), stream()) == 0
+    assert torch.equal(t, t1)
+    back3 = torch.empty(count * 8 * N, dtype=torch.float64, device="cuda")
+    back0 = torch.empty(count * 8 * N, dtype=torch.float64, device="cuda")
+    assert lib.lbm_warm_decode(count, nx, nx, 1, dx, 3, ptr(t), ptr(s), None, ptr(back3), 0,
+                               stream()) == 0
+    assert np.abs(back3.cpu().numpy().reshape(count, 8, N) - pops).max() <= \
+        1e-4 * np.abs(pops).max()
+    assert lib.lbm_warm_targets(count, nx, nx, dx, 4, ptr(dev(pops)), ptr(s), None,
                                 ptr(t), stream()) == lbm.LBM_ERR_ARG
+    assert lib.lbm_warm_decode(count, nx, nx, 1, dx, 4, ptr(t), ptr(s), None, ptr(back0), 0,
+                               stream()) == lbm.LBM_ERR_ARG
 
 
 def test_restriction_and_prolongation(lbm):
