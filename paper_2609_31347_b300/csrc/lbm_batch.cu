@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_batch(const double *__rest
   double p[8], gsel, o[8], ax, ay;
   pull_adjoint<false>(pin, x, y, g, b, p, gsel);
   const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
-  if (ARITH == 0 || !collide_T_fix<false>(p, rx, ry, c.fx, o, ax, ay))
+  if (ARITH == 0 || !collide_T_fix<false, false, true>(p, rx, ry, c.fx, o, ax, ay))
     collide_T<false>(p, rx, ry, c, o, ax, ay);
 #pragma unroll
   for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
