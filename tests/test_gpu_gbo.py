@@ -259,3 +259,31 @@ def test_distributed_gradient_central_fd_at_64_random_nodes(mods):
     # cancellation bound of central differences: a few eps |J| / h
     assert worst <= 10 * 2.2e-16 * abs(J0) / h + 1e-9 * np.abs(g).max(), (worst, J0)
     s.close()
+
+
+def test_plate_identification_error_on_the_paper_ladder(mods):
+    # Section 4.3.3 with Table 4 settings (E^(0) = 0.15, E* = 0.1, eps = 1e-10, solves capped
+    # at T_max = 60): the recovered control's error falls under refinement, at the order
+    # of the printed errors (2.23 % at N_x = 40, 0.55 % at N_x = 80).  The paper's boundary
+    # rules are not given and ours are first order of their own, so only the order of
+    # magnitude and the decrease are pinned (measured here: 6.5 % and 2.0 %).
+    lbm, gbo = mods
+    errs = []
+    for Nx, paper in ((40, 0.0223), (80, 0.0055)):
+        geo = I.plate_geometry(Nx)
+        dstar, sigma, F = I.plate_manufactured(geo.X, geo.Y)
+        wd, wT = I.plate_wall_data(geo)
+        s = lbm.LBMSolid(geo.nx, geo.nx, geo.dx, I.PLATE_E, I.PLATE_NU, periodic=False,
+                         node_mask=geo.active, link_bc=geo.link, wall_d=wd, wall_T=wT,
+                         wall_n=geo.normal, obs=geo.active.astype(float),
+                         control="young_scalar", force=F * geo.active)
+        s.set_target(dev(dstar))
+        opts = gbo.SolveOpts(tol=1e-10, max_steps=int(60 * Nx * Nx / 2.25))
+        r = gbo.lbfgs(gbo.make_fg(s, opts, opts), dev([np.sqrt(0.15)]), m_max=50, eps=1e-10,
+                      k_max=20)
+        a = abs(float(r.alpha[0]))
+        err = abs(a - np.sqrt(I.PLATE_E)) / np.sqrt(I.PLATE_E)
+        assert paper / 5 <= err <= 5 * paper, (Nx, err)
+        errs.append(err)
+        s.close()
+    assert errs[1] < 0.5 * errs[0]
