@@ -40,6 +40,15 @@ struct YoungDeriv {
   double dc11, dcs, dcd, dgam;
 };
 
+// Population loads.  NC = true: through the read-only (non-coherent) path, for kernels
+// that never write what they read; NC = false: coherent loads, for the cluster-resident
+// kernel, which rewrites its lattice between sweeps within one launch.
+template <bool NC>
+__device__ __forceinline__ double ldp(const double *p) {
+  if (NC) return __ldg(p);
+  return *p;
+}
+
 // Neighbour index with periodic wrap.
 __device__ __forceinline__ long wrap_idx(int x, int y, int dx_, int dy_, const Grid &g) {
   int xs = x + dx_, ys = y + dy_;
@@ -50,7 +59,7 @@ __device__ __forceinline__ long wrap_idx(int x, int y, int dx_, int dy_, const G
 
 // Post-streaming populations at (x, y): f_S,k(x) = f_C,k(x - c_k) (Eq. local_stream),
 // with the boundary rules at boundary nodes.  Returns false for outside nodes.
-template <bool BOUNDED>
+template <bool BOUNDED, bool NC = true>
 __device__ __forceinline__ bool pull_primal(const double *__restrict__ fin, int x, int y,
                                             const Grid &g, const Bounded &b, double (&f)[8],
                                             double &gam_sel) {
@@ -61,14 +70,14 @@ __device__ __forceinline__ bool pull_primal(const double *__restrict__ fin, int 
     const long rm = (long)(y == 0 ? g.ny - 1 : y - 1) * g.nx;
     const long rp = (long)(y == g.ny - 1 ? 0 : y + 1) * g.nx;
     const long r0 = (long)y * g.nx;
-    f[0] = __ldg(fin + 0 * g.N + r0 + xm);
-    f[1] = __ldg(fin + 1 * g.N + rm + x);
-    f[2] = __ldg(fin + 2 * g.N + r0 + xp);
-    f[3] = __ldg(fin + 3 * g.N + rp + x);
-    f[4] = __ldg(fin + 4 * g.N + rm + xm);
-    f[5] = __ldg(fin + 5 * g.N + rm + xp);
-    f[6] = __ldg(fin + 6 * g.N + rp + xp);
-    f[7] = __ldg(fin + 7 * g.N + rp + xm);
+    f[0] = ldp<NC>(fin + 0 * g.N + r0 + xm);
+    f[1] = ldp<NC>(fin + 1 * g.N + rm + x);
+    f[2] = ldp<NC>(fin + 2 * g.N + r0 + xp);
+    f[3] = ldp<NC>(fin + 3 * g.N + rp + x);
+    f[4] = ldp<NC>(fin + 4 * g.N + rm + xm);
+    f[5] = ldp<NC>(fin + 5 * g.N + rm + xp);
+    f[6] = ldp<NC>(fin + 6 * g.N + rp + xp);
+    f[7] = ldp<NC>(fin + 7 * g.N + rp + xm);
     return true;
   } else {
     const uint8_t t = b.type[n];
@@ -76,19 +85,19 @@ __device__ __forceinline__ bool pull_primal(const double *__restrict__ fin, int 
     if (t == 1) {
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+        f[k] = ldp<NC>(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
       return true;
     }
     const int bi = b.bidx[n];
     const unsigned reg = b.regmask[bi];
     double own[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) own[j] = __ldg(fin + j * g.N + n);
+    for (int j = 0; j < 8; ++j) own[j] = ldp<NC>(fin + j * g.N + n);
     const double *Q = b.Q + (long)bi * 64;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       if (reg & (1u << k)) {
-        f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+        f[k] = ldp<NC>(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
       } else {
         double acc = b.s[(long)bi * 8 + k];
 #pragma unroll
@@ -103,7 +112,7 @@ __device__ __forceinline__ bool pull_primal(const double *__restrict__ fin, int 
 
 // Adjoint streaming phi_S = S'^T phi_C at (x, y): phi_S,j(x) = phi_C,j(x + c_j) where
 // that node pulls from x, plus Q^T phi_C(x) at boundary nodes.
-template <bool BOUNDED>
+template <bool BOUNDED, bool NC = true>
 __device__ __forceinline__ bool pull_adjoint(const double *__restrict__ pin, int x, int y,
                                              const Grid &g, const Bounded &b, double (&p)[8],
                                              double &gam_sel) {
@@ -114,14 +123,14 @@ __device__ __forceinline__ bool pull_adjoint(const double *__restrict__ pin, int
     const long rm = (long)(y == 0 ? g.ny - 1 : y - 1) * g.nx;
     const long rp = (long)(y == g.ny - 1 ? 0 : y + 1) * g.nx;
     const long r0 = (long)y * g.nx;
-    p[0] = __ldg(pin + 0 * g.N + r0 + xp);
-    p[1] = __ldg(pin + 1 * g.N + rp + x);
-    p[2] = __ldg(pin + 2 * g.N + r0 + xm);
-    p[3] = __ldg(pin + 3 * g.N + rm + x);
-    p[4] = __ldg(pin + 4 * g.N + rp + xp);
-    p[5] = __ldg(pin + 5 * g.N + rp + xm);
-    p[6] = __ldg(pin + 6 * g.N + rm + xm);
-    p[7] = __ldg(pin + 7 * g.N + rm + xp);
+    p[0] = ldp<NC>(pin + 0 * g.N + r0 + xp);
+    p[1] = ldp<NC>(pin + 1 * g.N + rp + x);
+    p[2] = ldp<NC>(pin + 2 * g.N + r0 + xm);
+    p[3] = ldp<NC>(pin + 3 * g.N + rm + x);
+    p[4] = ldp<NC>(pin + 4 * g.N + rp + xp);
+    p[5] = ldp<NC>(pin + 5 * g.N + rp + xm);
+    p[6] = ldp<NC>(pin + 6 * g.N + rm + xm);
+    p[7] = ldp<NC>(pin + 7 * g.N + rm + xp);
     return true;
   } else {
     const uint8_t t = b.type[n];
@@ -129,21 +138,21 @@ __device__ __forceinline__ bool pull_adjoint(const double *__restrict__ pin, int
     if (t == 1) {
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        p[k] = __ldg(pin + k * g.N + n + kCX[k] + (long)kCY[k] * g.nx);
+        p[k] = ldp<NC>(pin + k * g.N + n + kCX[k] + (long)kCY[k] * g.nx);
       return true;
     }
     const int bi = b.bidx[n];
     const unsigned reg = b.regmask[bi];
     double own[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) own[k] = __ldg(pin + k * g.N + n);
+    for (int k = 0; k < 8; ++k) own[k] = ldp<NC>(pin + k * g.N + n);
     const double *Q = b.Q + (long)bi * 64;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       // downstream node x + c_j pulls f_C,j(x) iff its link j is regular, i.e. iff the
       // opposite link jbar at x is regular (its source x - c_jbar = x + c_j is active)
       const int jb = (j < 4) ? ((j + 2) & 3) : (((j - 4 + 2) & 3) + 4);
-      double acc = (reg & (1u << jb)) ? __ldg(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx)
+      double acc = (reg & (1u << jb)) ? ldp<NC>(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx)
                                       : 0.0;
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc += Q[k * 8 + j] * own[k];  // rows of regular links are 0
@@ -653,6 +662,7 @@ struct Compact {
 
 // Missing-link populations of boundary record bi at node n from its own post-collision
 // populations own[] (compact rule form); regular links pulled as usual.
+template <bool NC = true>
 __device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, long n,
                                                 const Grid &g, const Bounded &b,
                                                 const Compact &c, long bi,
@@ -661,7 +671,7 @@ __device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, 
   const unsigned neg = c.negmask[bi];
   double own[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) own[j] = __ldg(fin + j * g.N + n);
+  for (int j = 0; j < 8; ++j) own[j] = ldp<NC>(fin + j * g.N + n);
   const double mc11 = (own[4] - own[5]) + (own[6] - own[7]);
   const double mcs = ((own[0] + own[1]) + (own[2] + own[3])) +
                      2.0 * ((own[4] + own[5]) + (own[6] + own[7]));
@@ -669,7 +679,7 @@ __device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, 
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     if (reg & (1u << k)) {
-      f[k] = __ldg(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+      f[k] = ldp<NC>(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
     } else {
       const int kb = (k < 4) ? ((k + 2) & 3) : (((k - 4 + 2) & 3) + 4);
       const double *r = c.R + (long)(k * 4) * c.nb + bi;
@@ -683,6 +693,7 @@ __device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, 
 // Transposed pull of boundary record bi: phi_S,j(x) = [link jbar regular] phi_C,j(x + c_j)
 // + sigma_jbar [link jbar missing] phi_C,jbar(x) + sum_i t_i dm_i/df_j, with
 // t_i = sum over missing links k of r_ki phi_C,k(x) (the transpose of pull_boundary_c).
+template <bool NC = true>
 __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ pin, long n,
                                                     const Grid &g, const Bounded &b,
                                                     const Compact &c, long bi,
@@ -691,7 +702,7 @@ __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ p
   const unsigned neg = c.negmask[bi];
   double own[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) own[k] = __ldg(pin + k * g.N + n);
+  for (int k = 0; k < 8; ++k) own[k] = ldp<NC>(pin + k * g.N + n);
   double t11 = 0.0, ts = 0.0, td = 0.0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -708,7 +719,7 @@ __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ p
     const int jb = (j < 4) ? ((j + 2) & 3) : (((j - 4 + 2) & 3) + 4);
     double acc;
     if (reg & (1u << jb)) {
-      acc = __ldg(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx);
+      acc = ldp<NC>(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx);
     } else {
       acc = (neg & (1u << jb)) ? -own[jb] : own[jb];
     }
@@ -989,6 +1000,160 @@ __global__ void __launch_bounds__(256) k_adjoint_rest(const double *__restrict__
     pout[5 * g.N + n] = P2;
     pout[6 * g.N + n] = -P1;
     pout[7 * g.N + n] = -P2;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Cluster-resident sweeps for small lattices.  A lattice of a few thousand nodes is
+// latency-bound: each sweep launch costs more than its work.  One launch of a thread
+// block cluster (up to 16 CTAs, one GPC) runs a whole chunk of sweeps (the host uses it
+// for periodic lattices of up to 2048 nodes, where it measured faster); the sweeps are
+// ordered by the hardware cluster barrier with release / acquire semantics at cluster
+// scope, which makes every thread's writes of sweep s visible to every thread of the
+// cluster before sweep s + 1 reads them.  Populations are read with coherent loads
+// (they change within the launch); constants through the read-only path.
+//
+// Work items: periodic lattices, item = node; bounded grids, items [0, nb) are the
+// boundary records and [nb, nb + ninner) the interior nodes of `inner`.
+struct ClusterWork {
+  const int *inner;  // bounded: interior nodes
+  long nitems;
+};
+
+__device__ __forceinline__ void cluster_sync_release_acquire() {
+  asm volatile("barrier.cluster.arrive.release;\n\t"
+               "barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// One item of a primal sweep (coherent population loads); mon += |d|^2 if MON.
+template <bool BOUNDED, int ARITH, bool FIELD, bool MON>
+__device__ __forceinline__ void primal_item(const double *fin, double *fout,
+                                            const double *__restrict__ g2, const Grid &g,
+                                            const Bounded &b, const Compact &c,
+                                            const Coef &c0, const Field &fl,
+                                            const ClusterWork &w, long it, double &mon) {
+  double f[8], o[8], dxn = 0.0, dyn = 0.0;
+  long n;
+  if (BOUNDED && it < c.nb) {
+    n = c.bnode[it];
+    pull_boundary_c<false>(fin, n, g, b, c, it, f);
+    const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+    CoefFix cf;
+    if (ARITH == 0 || !node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, it, cf) ||
+        !collide_fix<MON, true>(f, qx, qy, cf, o, dxn, dyn))
+      collide<true>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, (int)it), o, dxn, dyn);
+  } else {
+    if (BOUNDED) {
+      n = w.inner[it - c.nb];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = fin[k * g.N + n - kCX[k] - (long)kCY[k] * g.nx];
+    } else {
+      n = it;
+      double gs;
+      pull_primal<false, false>(fin, (int)(n % g.nx), (int)(n / g.nx), g, b, f, gs);
+    }
+    const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+    if (ARITH == 0 ||
+        !collide_fix<MON>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
+      if (ARITH == 0 || !zero_node(f, qx, qy, o))
+        collide<false>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, -1), o, dxn, dyn);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
+  if (MON) mon += dxn * dxn + dyn * dyn;
+}
+
+// One item of an adjoint sweep (coherent loads); mon += |d^phi|^2 if MON.
+template <bool BOUNDED, int ARITH, bool FIELD, bool MON>
+__device__ __forceinline__ void adjoint_item(const double *pin, double *pout,
+                                             const double *__restrict__ r, const Grid &g,
+                                             const Bounded &b, const Compact &c,
+                                             const Coef &c0, const Field &fl,
+                                             const ClusterWork &w, long it, double &mon) {
+  double p[8], o[8], ax = 0.0, ay = 0.0;
+  long n;
+  if (BOUNDED && it < c.nb) {
+    n = c.bnode[it];
+    pull_boundary_adj_c<false>(pin, n, g, b, c, it, p);
+    const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
+    CoefFix cf;
+    if (ARITH == 0 || !node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, it, cf) ||
+        !collide_T_fix<MON, true>(p, rx, ry, cf, o, ax, ay))
+      collide_T<true>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, (int)it), o, ax, ay);
+  } else {
+    if (BOUNDED) {
+      n = w.inner[it - c.nb];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) p[k] = pin[k * g.N + n + kCX[k] + (long)kCY[k] * g.nx];
+    } else {
+      n = it;
+      double gs;
+      pull_adjoint<false, false>(pin, (int)(n % g.nx), (int)(n / g.nx), g, b, p, gs);
+    }
+    const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
+    if (ARITH == 0 ||
+        !collide_T_fix<MON>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
+      if (ARITH == 0 || !zero_node(p, rx, ry, o))
+        collide_T<false>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, -1), o, ax, ay);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
+  if (MON) mon += ax * ax + ay * ay;
+}
+
+// `nsweeps` sweeps (KIND 0 primal, 1 adjoint) from buffer a (the state) to a or b
+// (b after an odd count).  With monitor, the last sweep's partial sums of |d|^2 go to
+// partial[rank] and partial[ncta .. npartial) are zeroed, so the usual finishing pass
+// over npartial entries gives the monitor.  Launched as ONE cluster of gridDim.x CTAs.
+template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
+__global__ void __launch_bounds__(512) k_sweeps_cl(double *a, double *b2,
+                                                    const double *__restrict__ src2, Grid g,
+                                                    Bounded b, Compact c, Coef c0, Field fl,
+                                                    ClusterWork w, int nsweeps, int monitor,
+                                                    double *__restrict__ partial,
+                                                    long npartial) {
+  const unsigned rank = cluster_rank(), ncta = cluster_size();
+  const long T = (long)ncta * blockDim.x;
+  const long t0 = (long)rank * blockDim.x + threadIdx.x;
+  double mon[1] = {0.0};
+  for (int s = 0; s < nsweeps; ++s) {
+    const double *in = (s & 1) ? b2 : a;
+    double *out = (s & 1) ? a : b2;
+    if (monitor && s == nsweeps - 1) {
+      for (long it = t0; it < w.nitems; it += T) {
+        if (KIND == 0)
+          primal_item<BOUNDED, ARITH, FIELD, true>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
+        else
+          adjoint_item<BOUNDED, ARITH, FIELD, true>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
+      }
+    } else {
+      for (long it = t0; it < w.nitems; it += T) {
+        if (KIND == 0)
+          primal_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
+        else
+          adjoint_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
+      }
+    }
+    cluster_sync_release_acquire();
+  }
+  if (monitor) {
+    __shared__ double sm[32];
+    block_sum<1>(mon, sm);
+    if (threadIdx.x == 0) partial[rank] = mon[0];
+    if (rank == 0)
+      for (long i = (long)ncta + threadIdx.x; i < npartial; i += blockDim.x) partial[i] = 0.0;
   }
 }
 

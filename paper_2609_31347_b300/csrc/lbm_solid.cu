@@ -52,6 +52,9 @@ struct lbm_solid {
   double *R = nullptr;
   long cblocks = 0;
   long nmon = 0;  // blocks that write monitor partials in a sweep
+  // cluster-resident sweeps of small periodic lattices (0 CTAs: not used)
+  ClusterWork cw{};
+  int cl_ncta = 0, cl_threads = 0;
   Field fl{};
   bool field = false;
   // CUDA graphs of sweep chunks (launch overhead dominates small lattices): captured on
@@ -244,6 +247,76 @@ void launch_collide_only(lbm_solid *h) {
     k_collide_only<true, A, F><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->fnext, h->g2, h->grid, h->bnd, h->coef, h->fl);
 }
 
+// ---- cluster-resident sweeps ---------------------------------------------------------
+// Measured on B300 (time to gradient, us per sweep, cluster vs graph-replayed launches):
+// periodic 10^2 .. 40^2: 2.15-2.35 vs 2.6-2.8; 80^2: 4.0 vs 2.8; plates at N_x = 64: no
+// gain; 128^2 plate with a modulus field: 8.4 vs 6.6.  Inside one launch a sweep still
+// costs an L2 round trip plus the cluster barrier (~2 us); only the smallest lattices,
+// where a graph launch costs more than that, gain.  So: periodic lattices up to 2048
+// nodes.
+constexpr long kClusterMaxItems = 2048;
+constexpr int kClusterMaxCta = 16;            // one GPC (non-portable cluster size)
+constexpr long kClusterChunk = 512;           // sweeps per launch (fixed-step runs)
+
+template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
+cudaError_t launch_cluster(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
+                           int *fits = nullptr) {
+  auto kern = k_sweeps_cl<KIND, BOUNDED, ARITH, FIELD>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)h->cl_ncta);
+  cfg.blockDim = dim3((unsigned)h->cl_threads);
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)h->cl_ncta;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (probe) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveClusters(fits, kern, &cfg);
+  }
+  double *a = KIND == 0 ? h->fcur : h->pcur, *b = KIND == 0 ? h->fnext : h->pnext;
+  const double *src = KIND == 0 ? h->g2 : h->r2;
+  return cudaLaunchKernelEx(&cfg, kern, a, b, src, h->grid, h->bnd, h->cmp, h->coef, h->fl,
+                            h->cw, nsweeps, monitor ? 1 : 0, h->partial, h->nmon);
+}
+
+// (periodic lattices only: bounded grids measured no gain, see kClusterMaxItems)
+template <int KIND>
+cudaError_t launch_cluster_any(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
+                               int *fits = nullptr) {
+  const bool fp = h->kernel == LBM_KERNEL_FP64;
+  if (h->field)
+    return fp ? launch_cluster<KIND, false, 0, true>(h, nsweeps, monitor, probe, fits)
+              : launch_cluster<KIND, false, 1, true>(h, nsweeps, monitor, probe, fits);
+  return fp ? launch_cluster<KIND, false, 0, false>(h, nsweeps, monitor, probe, fits)
+            : launch_cluster<KIND, false, 1, false>(h, nsweeps, monitor, probe, fits);
+}
+
+// Chooses the cluster shape for a small lattice (CTAs of whole warps, about one item per
+// thread, as many CTAs as a GPC allows) and checks that such a cluster can be scheduled;
+// otherwise the handle keeps the graph-replayed launches.
+void setup_cluster(lbm_solid *h, long items) {
+  h->cl_ncta = 0;
+  if (items < 1 || items > kClusterMaxItems) return;
+  for (int ncta = (int)std::min<long>(kClusterMaxCta, (items + 31) / 32); ncta >= 1; ncta /= 2) {
+    const long per = (items + ncta - 1) / ncta;
+    h->cl_ncta = ncta;
+    h->cl_threads = (int)std::min<long>(512, (per + 31) / 32 * 32);
+    int f0 = 0, f1 = 0;
+    if (launch_cluster_any<0>(h, 0, false, true, &f0) == cudaSuccess && f0 > 0 &&
+        launch_cluster_any<1>(h, 0, false, true, &f1) == cudaSuccess && f1 > 0) {
+      if (h->nmon < ncta) h->nmon = ncta;
+      return;
+    }
+    cudaGetLastError();  // clear a refused configuration, try a smaller cluster
+  }
+  h->cl_ncta = 0;
+}
+
 // Kernel variant of a sweep: FP64 pipe for LBM_KERNEL_FP64, fixed-point bulk nodes
 // otherwise; per-node constants for modulus fields.
 void launch_primal_any(lbm_solid *h, bool monitor) {
@@ -365,6 +438,23 @@ lbm_status run_sweeps(lbm_solid *h, int kind, long k, bool mon) {
     std::swap(h->pcur, h->pnext);
     h->pcur_rest = false;
     --k;
+  }
+  if (h->cl_ncta > 0) {  // small lattice: cluster-resident launches of up to 512 sweeps
+    while (k > 0) {
+      const long c = k > kClusterChunk ? kClusterChunk : k;
+      const bool m = mon && c == k;
+      const cudaError_t e = kind == 0 ? launch_cluster_any<0>(h, (int)c, m)
+                                      : launch_cluster_any<1>(h, (int)c, m);
+      if (e != cudaSuccess)
+        return fail(h, LBM_ERR_CUDA, std::string("cluster launch: ") + cudaGetErrorString(e));
+      LAUNCHED(h);
+      if (c & 1) {
+        if (kind == 0) std::swap(h->fcur, h->fnext);
+        else std::swap(h->pcur, h->pnext);
+      }
+      k -= c;
+    }
+    return LBM_OK;
   }
   while (k > 0) {
     long c = k > kGraphMax ? kGraphMax : k;
@@ -775,6 +865,10 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
     if (cudaGetLastError() != cudaSuccess) return bail(LBM_ERR_CUDA);
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(LBM_ERR_CUDA);
+  if (h->periodic) {
+    h->cw = ClusterWork{nullptr, N};
+    setup_cluster(h, N);
+  }
   *out = h;
   return LBM_OK;
 }
