@@ -60,7 +60,10 @@ __device__ __forceinline__ long long to_fix(double x, int sh20) {
 // (e = 0) give 0.  The primal collision converts its two force values this way and its
 // eight populations with to_fix, which moves work from the FP64 pipe (which runs the
 // conversion instruction) to the integer pipes (measured: primal sweep 0.411 -> 0.406
-// ms at 4096^2; the transposed collision, slower that way, keeps to_fix throughout).
+// ms at 4096^2; the transposed collision, slower that way, keeps to_fix for bulk nodes).
+// Boundary nodes (BND) convert all ten inputs this way: their rules already load the
+// FP64 pipe, and a boundary warp is the critical path of a small plate's sweep
+// (measured 2-4 % per sweep at N_x = 64 .. 512).
 __device__ __forceinline__ long long to_fix_alu(double x, int E) {
   const long long b = __double_as_longlong(x);
   const int e = (int)(b >> 52) & 0x7ff;
@@ -121,7 +124,7 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
   const int sh20 = (1079 - E) << 20;
   long long F[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) F[k] = to_fix(f[k], sh20);
+  for (int k = 0; k < 8; ++k) F[k] = BND ? to_fix_alu(f[k], E) : to_fix(f[k], sh20);
   const long long QX = to_fix_alu(qx, E), QY = to_fix_alu(qy, E);
   const long long a1 = F[0] + F[2], b1 = F[0] - F[2];
   const long long a2 = F[1] + F[3], b2 = F[1] - F[3];
@@ -175,9 +178,9 @@ __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, d
   const int sh20 = (1079 - E) << 20;
   long long P[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) P[k] = to_fix(p[k], sh20);
-  const long long RX = ALU_SRC ? to_fix_alu(rx, E) : to_fix(rx, sh20);
-  const long long RY = ALU_SRC ? to_fix_alu(ry, E) : to_fix(ry, sh20);
+  for (int k = 0; k < 8; ++k) P[k] = BND ? to_fix_alu(p[k], E) : to_fix(p[k], sh20);
+  const long long RX = (ALU_SRC || BND) ? to_fix_alu(rx, E) : to_fix(rx, sh20);
+  const long long RY = (ALU_SRC || BND) ? to_fix_alu(ry, E) : to_fix(ry, sh20);
   const long long A1 = P[0] + P[2], B1 = P[0] - P[2];
   const long long A2 = P[1] + P[3], B2 = P[1] - P[3];
   const long long A3 = P[4] + P[6], B3 = P[4] - P[6];

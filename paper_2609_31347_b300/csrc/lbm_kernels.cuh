@@ -645,10 +645,12 @@ __global__ void k_subtract_mean(double *__restrict__ v, const double *__restrict
 // Compact launch of a bounded grid.  The box is mostly outside the domain, and a warp
 // that holds one boundary node runs that node's rule and gamma-modified collision on
 // the FP64 pipe for all its lanes.  So the sweep launches only active nodes: first
-// kBndBlocks blocks of boundary nodes packed one per thread (they take longest, so
+// `bblocks` blocks of boundary nodes packed one per thread (they take longest, so
 // they start first), then the interior nodes as warp-sized chunks of up to 32
 // consecutive nodes of one row (every pull of such a warp is a contiguous, coalesced
-// access).  Interior nodes have all eight links regular.
+// access).  Interior nodes have all eight links regular.  A block holds blockDim.x
+// boundary records or blockDim.x / 32 chunks; every kernel of one compact layout is
+// launched with the same block size (a multiple of 32, at most kCompactThreads).
 constexpr int kCompactThreads = 128;
 
 struct Compact {
@@ -661,8 +663,12 @@ struct Compact {
 };
 
 // Missing-link populations of boundary record bi at node n from its own post-collision
-// populations own[] (compact rule form); regular links pulled as usual.
-template <bool NC = true>
+// populations own[] (compact rule form); regular links pulled as usual.  HOIST issues
+// every load of the record (own and pulled populations, the rule coefficients of all
+// missing links) before the first arithmetic: one L2 round trip instead of one per
+// missing link (a rule's coefficients are otherwise loaded inside its branch and used
+// at once), for more registers; the host takes it where the sweep is latency-bound.
+template <bool NC = true, bool HOIST = false>
 __device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, long n,
                                                 const Grid &g, const Bounded &b,
                                                 const Compact &c, long bi,
@@ -672,6 +678,35 @@ __device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, 
   double own[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) own[j] = ldp<NC>(fin + j * g.N + n);
+  if (HOIST) {
+    double rk[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (reg & (1u << k)) {
+        f[k] = ldp<NC>(fin + k * g.N + n - kCX[k] - (long)kCY[k] * g.nx);
+        rk[k][0] = rk[k][1] = rk[k][2] = rk[k][3] = 0.0;
+      } else {
+        const double *r = c.R + (long)(k * 4) * c.nb + bi;
+        rk[k][0] = __ldg(r);
+        rk[k][1] = __ldg(r + c.nb);
+        rk[k][2] = __ldg(r + 2 * c.nb);
+        rk[k][3] = __ldg(r + 3 * c.nb);
+      }
+    }
+    const double mc11 = (own[4] - own[5]) + (own[6] - own[7]);
+    const double mcs = ((own[0] + own[1]) + (own[2] + own[3])) +
+                       2.0 * ((own[4] + own[5]) + (own[6] + own[7]));
+    const double mcd = (own[0] - own[1]) + (own[2] - own[3]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (!(reg & (1u << k))) {
+        const int kb = (k < 4) ? ((k + 2) & 3) : (((k - 4 + 2) & 3) + 4);
+        const double ob = (neg & (1u << k)) ? -own[kb] : own[kb];
+        f[k] = fma(rk[k][0], mc11, fma(rk[k][1], mcs, fma(rk[k][2], mcd, ob + rk[k][3])));
+      }
+    }
+    return;
+  }
   const double mc11 = (own[4] - own[5]) + (own[6] - own[7]);
   const double mcs = ((own[0] + own[1]) + (own[2] + own[3])) +
                      2.0 * ((own[4] + own[5]) + (own[6] + own[7]));
@@ -693,7 +728,7 @@ __device__ __forceinline__ void pull_boundary_c(const double *__restrict__ fin, 
 // Transposed pull of boundary record bi: phi_S,j(x) = [link jbar regular] phi_C,j(x + c_j)
 // + sigma_jbar [link jbar missing] phi_C,jbar(x) + sum_i t_i dm_i/df_j, with
 // t_i = sum over missing links k of r_ki phi_C,k(x) (the transpose of pull_boundary_c).
-template <bool NC = true>
+template <bool NC = true, bool HOIST = false>
 __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ pin, long n,
                                                     const Grid &g, const Bounded &b,
                                                     const Compact &c, long bi,
@@ -704,13 +739,40 @@ __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ p
 #pragma unroll
   for (int k = 0; k < 8; ++k) own[k] = ldp<NC>(pin + k * g.N + n);
   double t11 = 0.0, ts = 0.0, td = 0.0;
+  double pv[8];  // HOIST: the regular links' pulled values, loaded up front
+  if (HOIST) {  // all loads first (see pull_boundary_c)
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (!(reg & (1u << k))) {
+    for (int j = 0; j < 8; ++j) {
+      const int jb = (j < 4) ? ((j + 2) & 3) : (((j - 4 + 2) & 3) + 4);
+      pv[j] = (reg & (1u << jb)) ? ldp<NC>(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx)
+                                 : 0.0;
+    }
+    double rk[8][3];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
       const double *r = c.R + (long)(k * 4) * c.nb + bi;
-      t11 = fma(__ldg(r), own[k], t11);
-      ts = fma(__ldg(r + c.nb), own[k], ts);
-      td = fma(__ldg(r + 2 * c.nb), own[k], td);
+      const bool miss = !(reg & (1u << k));
+      rk[k][0] = miss ? __ldg(r) : 0.0;
+      rk[k][1] = miss ? __ldg(r + c.nb) : 0.0;
+      rk[k][2] = miss ? __ldg(r + 2 * c.nb) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (!(reg & (1u << k))) {
+        t11 = fma(rk[k][0], own[k], t11);
+        ts = fma(rk[k][1], own[k], ts);
+        td = fma(rk[k][2], own[k], td);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (!(reg & (1u << k))) {
+        const double *r = c.R + (long)(k * 4) * c.nb + bi;
+        t11 = fma(__ldg(r), own[k], t11);
+        ts = fma(__ldg(r + c.nb), own[k], ts);
+        td = fma(__ldg(r + 2 * c.nb), own[k], td);
+      }
     }
   }
   const double ax = ts + td, ay = ts - td, d1 = 2.0 * ts + t11, d2 = 2.0 * ts - t11;
@@ -719,7 +781,7 @@ __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ p
     const int jb = (j < 4) ? ((j + 2) & 3) : (((j - 4 + 2) & 3) + 4);
     double acc;
     if (reg & (1u << jb)) {
-      acc = ldp<NC>(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx);
+      acc = HOIST ? pv[j] : ldp<NC>(pin + j * g.N + n + kCX[j] + (long)kCY[j] * g.nx);
     } else {
       acc = (neg & (1u << jb)) ? -own[jb] : own[jb];
     }
@@ -731,7 +793,7 @@ __device__ __forceinline__ void pull_boundary_adj_c(const double *__restrict__ p
 
 // The per-thread work of a primal sweep of a bounded grid (compact launch, block
 // blockIdx.x); mon receives |d|^2 of the thread's node (0 if none).
-template <bool MONITOR, int ARITH, bool FIELD>
+template <bool MONITOR, int ARITH, bool FIELD, bool HOIST = false>
 __device__ __forceinline__ void sweep_primal_c(const double *__restrict__ fin,
                                                double *__restrict__ fout,
                                                const double *__restrict__ g2, const Grid &g,
@@ -739,22 +801,31 @@ __device__ __forceinline__ void sweep_primal_c(const double *__restrict__ fin,
                                                const Coef &c0, const Field &fl, double &mon) {
   mon = 0.0;
   if ((int)blockIdx.x < c.bblocks) {
-    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    const long bi = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (bi < c.nb) {
       const long n = c.bnode[bi];
-      double f[8], o[8], dxn = 0.0, dyn = 0.0;
-      pull_boundary_c(fin, n, g, b, c, bi, f);
-      const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
+      double f[8], o[8], dxn = 0.0, dyn = 0.0, qx, qy;
       CoefFix cf;
-      if (ARITH == 0 || !node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf) ||
-          !collide_fix<MONITOR, true>(f, qx, qy, cf, o, dxn, dyn))
+      bool fix_ok;
+      if (HOIST) {  // the node's other loads before the pull's arithmetic as well
+        qx = __ldg(g2 + n);
+        qy = __ldg(g2 + g.N + n);
+        fix_ok = ARITH != 0 && node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf);
+        pull_boundary_c<true, true>(fin, n, g, b, c, bi, f);
+      } else {
+        pull_boundary_c<true, false>(fin, n, g, b, c, bi, f);
+        qx = __ldg(g2 + n);
+        qy = __ldg(g2 + g.N + n);
+        fix_ok = ARITH != 0 && node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf);
+      }
+      if (!fix_ok || !collide_fix<MONITOR, true>(f, qx, qy, cf, o, dxn, dyn))
         collide<true>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, (int)bi), o, dxn, dyn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
       if (MONITOR) mon = dxn * dxn + dyn * dyn;
     }
   } else {
-    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const long w = ((long)(blockIdx.x - c.bblocks) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w < c.nchunk) {
       const int2 ch = c.chunk[w];
@@ -780,7 +851,7 @@ __device__ __forceinline__ void sweep_primal_c(const double *__restrict__ fin,
 }
 
 // One primal sweep of a bounded grid (compact launch); monitor partial per block.
-template <bool MONITOR, int ARITH, bool FIELD>
+template <bool MONITOR, int ARITH, bool FIELD, bool HOIST>
 __global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__restrict__ fin,
                                                               double *__restrict__ fout,
                                                               const double *__restrict__ g2,
@@ -788,7 +859,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_primal_c(const double *__re
                                                               Coef c0, Field fl,
                                                               double *__restrict__ partial) {
   double mon[1];
-  sweep_primal_c<MONITOR, ARITH, FIELD>(fin, fout, g2, g, b, c, c0, fl, mon[0]);
+  sweep_primal_c<MONITOR, ARITH, FIELD, HOIST>(fin, fout, g2, g, b, c, c0, fl, mon[0]);
   if (MONITOR) {
     __shared__ double sm[32];
     block_sum<1>(mon, sm);
@@ -835,10 +906,10 @@ __global__ void __launch_bounds__(kCompactThreads) k_collide_cb(const double *__
   fout += 8 * g.N * i;
   long n = -1, bi = -1;
   if ((int)blockIdx.x < c.bblocks) {
-    bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    bi = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (bi < c.nb) n = c.bnode[bi];
   } else {
-    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const long w = ((long)(blockIdx.x - c.bblocks) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w < c.nchunk) {
       const int2 ch = c.chunk[w];
@@ -874,14 +945,14 @@ static __global__ void __launch_bounds__(kCompactThreads) k_pull_cb(
   fs += 8 * g.N * i;
   double f[8];
   if ((int)blockIdx.x < c.bblocks) {
-    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    const long bi = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (bi >= c.nb) return;
     const long n = c.bnode[bi];
     pull_boundary_c(fin, n, g, b, c, bi, f);
 #pragma unroll
     for (int k = 0; k < 8; ++k) fs[k * g.N + n] = f[k];
   } else {
-    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const long w = ((long)(blockIdx.x - c.bblocks) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= c.nchunk) return;
     const int2 ch = c.chunk[w];
@@ -893,7 +964,7 @@ static __global__ void __launch_bounds__(kCompactThreads) k_pull_cb(
 }
 
 // One adjoint sweep of a bounded grid (compact launch).
-template <bool MONITOR, int ARITH, bool FIELD>
+template <bool MONITOR, int ARITH, bool FIELD, bool HOIST>
 __global__ void __launch_bounds__(kCompactThreads) k_adjoint_c(const double *__restrict__ pin,
                                                                double *__restrict__ pout,
                                                                const double *__restrict__ r,
@@ -902,22 +973,31 @@ __global__ void __launch_bounds__(kCompactThreads) k_adjoint_c(const double *__r
                                                                double *__restrict__ partial) {
   double mon[1] = {0.0};
   if ((int)blockIdx.x < c.bblocks) {
-    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    const long bi = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (bi < c.nb) {
       const long n = c.bnode[bi];
-      double p[8], o[8], ax = 0.0, ay = 0.0;
-      pull_boundary_adj_c(pin, n, g, b, c, bi, p);
-      const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
+      double p[8], o[8], ax = 0.0, ay = 0.0, rx, ry;
       CoefFix cf;
-      if (ARITH == 0 || !node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf) ||
-          !collide_T_fix<MONITOR, true>(p, rx, ry, cf, o, ax, ay))
+      bool fix_ok;
+      if (HOIST) {
+        rx = __ldg(r + n);
+        ry = __ldg(r + g.N + n);
+        fix_ok = ARITH != 0 && node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf);
+        pull_boundary_adj_c<true, true>(pin, n, g, b, c, bi, p);
+      } else {
+        pull_boundary_adj_c<true, false>(pin, n, g, b, c, bi, p);
+        rx = __ldg(r + n);
+        ry = __ldg(r + g.N + n);
+        fix_ok = ARITH != 0 && node_fix_bnd<FIELD>(c0.fx, fl, g.N, n, bi, cf);
+      }
+      if (!fix_ok || !collide_T_fix<MONITOR, true>(p, rx, ry, cf, o, ax, ay))
         collide_T<true>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, (int)bi), o, ax, ay);
 #pragma unroll
       for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
       if (MONITOR) mon[0] = ax * ax + ay * ay;
     }
   } else {
-    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const long w = ((long)(blockIdx.x - c.bblocks) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w < c.nchunk) {
       const int2 ch = c.chunk[w];
@@ -953,10 +1033,10 @@ static __global__ void __launch_bounds__(kCompactThreads) k_residual_c(
   double v[2] = {0.0, 0.0};
   long n = -1;
   if ((int)blockIdx.x < c.bblocks) {
-    const long bi = (long)blockIdx.x * kCompactThreads + threadIdx.x;
+    const long bi = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (bi < c.nb) n = c.bnode[bi];
   } else {
-    const long w = ((long)(blockIdx.x - c.bblocks) * kCompactThreads + threadIdx.x) >> 5;
+    const long w = ((long)(blockIdx.x - c.bblocks) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w < c.nchunk) {
       const int2 ch = c.chunk[w];
