@@ -88,6 +88,33 @@ def test_plate_primal_adjoint_force_gradient(lbm_mod, Nx, E, nu, steps, kernel):
     s.close()
 
 
+@pytest.mark.parametrize("kernel", ["fp64", "auto"])
+def test_large_plate_wide_compact_layout_matches_the_oracle(lbm_mod, kernel):
+    # N_x = 600 (601^2 box): 5.7 k warps of compact work, above 32 per SM, so the sweeps
+    # run 128-thread blocks without the hoisted boundary loads; the smaller plates above
+    # run 32-thread blocks with them.  A random start puts every node on the bulk paths.
+    Nx, E, nu, steps = 600, I.PLATE_E, I.PLATE_NU, 25
+    geo, dstar, F, wd, wT = paper_plate(Nx)
+    rng = np.random.default_rng(11)
+    f0 = rng.standard_normal((8, geo.nx * geo.nx)) * 1e-3 * geo.active
+    s = make(lbm_mod, geo, wd, wT, E, nu, kernel=kernel)
+    s.set_target(dev(dstar))
+    s.set_control(dev(F))
+    s.set_populations(0, dev(f0))
+    s.primal_solve(steps, fixed_steps=True)
+    g = ogrid(geo, wd, wT, nu)
+    fS = oracle.primal(g, E, F, steps, fS0=f0)
+    assert rel_inf(host(s.get_populations(0)).reshape(8, -1), fS) <= POP_TOL
+    obs = geo.active.astype(float)
+    s.objective()
+    s.adjoint_solve(steps, fixed_steps=True)
+    phiC, phiS = oracle.adjoint(g, E, F, fS, dstar, steps, obs=obs)
+    assert rel_inf(host(s.get_populations(2)).reshape(8, -1), phiC) <= POP_TOL
+    gref = oracle.gradient_force(g, E, F, fS, phiS, dstar, obs=obs)
+    assert rel_inf(host(s.gradient()).reshape(2, -1), gref) <= GRAD_TOL
+    s.close()
+
+
 @pytest.mark.parametrize("Nx,E0", [(12, 0.15), (16, 0.07)])
 def test_plate_young_gradient_matches_oracle_and_fad(lbm_mod, Nx, E0):
     # Benchmark (3): E = alpha^2 with loads fixed at the reference modulus (E* = 0.1)
