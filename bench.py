@@ -311,6 +311,24 @@ def batch_throughput(torch, lbm, I, count: int = 256, sweeps: int = 20, seed: in
            "adjoint_hbm_gbs": BYTES_PER_LUP * b.total / (ta * 1e-3) / 1e9,
            "adjoint_call_ms_per_sweep": tcall}
     b.close()
+    # the per-sweep launch floor: a tiny batch (4 x 64^2) replays the same graphs of
+    # one launch per sweep; its sweep time bounds what a persistent kernel could save
+    small = lbm.LBMBatch([(64, 64)] * 4, 8.0 / 3.0, 1.0 / 3.0)
+    Fs = 1e-3 * torch.randn(2 * small.total, dtype=torch.float64, device="cuda")
+    small.set_target(1e-2 * torch.randn_like(Fs))
+    small.set_force(Fs)
+    for _ in range(2):
+        small.primal(512)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    small.primal(512)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    floor_us = e[0].elapsed_time(e[1]) / 512 * 1e3
+    small.close()
+    out["launch_floor_us_per_sweep"] = floor_us
+    out["launch_floor_share_of_sweep"] = floor_us * 1e-3 / tp
     return out
 
 

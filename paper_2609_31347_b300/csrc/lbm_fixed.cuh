@@ -114,8 +114,9 @@ __device__ __forceinline__ int max_exp10(const double (&f)[8], double a, double 
 
 // Collision in fixed point (same map as collide<BND>; boundary rows use qs_b, P_b).
 // Returns false when the node must take the FP64-pipe path (largest exponent outside
-// [kEmin, kEmax]).
-template <bool MON, bool BND = false>
+// [kEmin, kEmax]).  ALU_POP converts the eight populations on the integer pipes as well
+// (the same values: both conversions truncate the same product).
+template <bool MON, bool BND = false, bool ALU_POP = BND>
 __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, double qy,
                                             const CoefFix &c, double (&o)[8], double &dx_,
                                             double &dy_) {
@@ -124,7 +125,7 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
   const int sh20 = (1079 - E) << 20;
   long long F[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) F[k] = BND ? to_fix_alu(f[k], E) : to_fix(f[k], sh20);
+  for (int k = 0; k < 8; ++k) F[k] = ALU_POP ? to_fix_alu(f[k], E) : to_fix(f[k], sh20);
   const long long QX = to_fix_alu(qx, E), QY = to_fix_alu(qy, E);
   const long long a1 = F[0] + F[2], b1 = F[0] - F[2];
   const long long a2 = F[1] + F[3], b2 = F[1] - F[3];
@@ -169,7 +170,7 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
 // two source values on the integer pipes (to_fix_alu) instead of the FP64 pipe: measured
 // faster for the batched adjoint (2.59 -> 2.50 ms per sweep of 97 M nodes), slower for one
 // 4096^2 lattice (0.388 -> 0.392 ms), so each kernel picks.
-template <bool MON, bool BND = false, bool ALU_SRC = false>
+template <bool MON, bool BND = false, bool ALU_SRC = false, bool ALU_POP = BND>
 __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, double ry,
                                               const CoefFix &c, double (&o)[8], double &ax,
                                               double &ay) {
@@ -178,9 +179,9 @@ __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, d
   const int sh20 = (1079 - E) << 20;
   long long P[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) P[k] = BND ? to_fix_alu(p[k], E) : to_fix(p[k], sh20);
-  const long long RX = (ALU_SRC || BND) ? to_fix_alu(rx, E) : to_fix(rx, sh20);
-  const long long RY = (ALU_SRC || BND) ? to_fix_alu(ry, E) : to_fix(ry, sh20);
+  for (int k = 0; k < 8; ++k) P[k] = ALU_POP ? to_fix_alu(p[k], E) : to_fix(p[k], sh20);
+  const long long RX = (ALU_SRC || ALU_POP) ? to_fix_alu(rx, E) : to_fix(rx, sh20);
+  const long long RY = (ALU_SRC || ALU_POP) ? to_fix_alu(ry, E) : to_fix(ry, sh20);
   const long long A1 = P[0] + P[2], B1 = P[0] - P[2];
   const long long A2 = P[1] + P[3], B2 = P[1] - P[3];
   const long long A3 = P[4] + P[6], B3 = P[4] - P[6];

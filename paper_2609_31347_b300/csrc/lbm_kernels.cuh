@@ -1237,6 +1237,121 @@ __global__ void __launch_bounds__(512) k_sweeps_cl(double *a, double *b2,
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Lattice resident in distributed shared memory (periodic lattices, uniform material).
+// One cluster of C CTAs holds the whole lattice: CTA q owns rows [q h, (q + 1) h) (h =
+// ny / C) in its shared memory, two population buffers (8 planes of h nx values each,
+// SoA) and the node's force or adjoint source (2 planes).  A sweep reads the pulled
+// populations of its own rows from its shared memory and those of the rows just above
+// and below its band from the neighbouring CTA's (mapa + ld.shared::cluster), writes the
+// other buffer, and ends at the cluster barrier (release / acquire), so no sweep touches
+// L2.  The state is read from global memory once at the start and written back at the
+// end: the final state to `a` (even count) or `b2` (odd), the one before it to the other,
+// as the graph-replayed sweeps leave them.  Populations are converted on the integer
+// pipes (a CTA holds few warps, and a lone warp's FP64 instruction costs 64 cycles).
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ double ld_cluster(unsigned local_addr, unsigned rank) {
+  unsigned remote;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+// Dynamic shared memory of k_sweeps_dsm: 18 doubles per node of the band.
+constexpr int kDsmDoublesPerNode = 18;
+
+template <int KIND, int ARITH>
+__global__ void __launch_bounds__(1024) k_sweeps_dsm(double *a, double *b2,
+                                                     const double *__restrict__ src2, Grid g,
+                                                     Coef c0, int h, int nsweeps, int monitor,
+                                                     double *__restrict__ partial,
+                                                     long npartial) {
+  extern __shared__ __align__(16) double dsm[];
+  const unsigned rank = cluster_rank(), C = cluster_size();
+  const int nx = g.nx;
+  const long L = (long)h * nx;
+  const long base = (long)rank * L;  // first node of the band (rows are contiguous)
+  double *B0 = dsm, *B1 = dsm + 8 * L, *Q = dsm + 16 * L;
+  for (long l = threadIdx.x; l < L; l += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) B0[k * L + l] = a[k * g.N + base + l];
+    Q[l] = src2[base + l];
+    Q[L + l] = src2[g.N + base + l];
+  }
+  const unsigned up = (rank + 1) % C, down = (rank + C - 1) % C;
+  double mon[1] = {0.0};
+  cluster_sync_release_acquire();
+  for (int s = 0; s < nsweeps; ++s) {
+    const double *S = (s & 1) ? B1 : B0;
+    double *D = (s & 1) ? B0 : B1;
+    const unsigned Sa = smem_addr(S);
+    const bool last_mon = monitor && s == nsweeps - 1;
+    for (long l = threadIdx.x; l < L; l += blockDim.x) {
+      const int x = (int)(l % nx), yl = (int)(l / nx);
+      // source of link k: primal pulls from x - c_k, the adjoint from x + c_k; rows
+      // outside the band belong to the neighbouring CTA (|c_y| <= 1)
+      const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+      double f[8], o[8], m1 = 0.0, m2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int dx = KIND == 0 ? -kCX[k] : kCX[k], dy = KIND == 0 ? -kCY[k] : kCY[k];
+        const int sx = dx < 0 ? xm : (dx > 0 ? xp : x);
+        const int sy = yl + dy;
+        if (sy >= 0 && sy < h) {
+          f[k] = S[k * L + (long)sy * nx + sx];
+        } else {
+          const long off = k * L + (long)(sy < 0 ? h - 1 : 0) * nx + sx;
+          f[k] = ld_cluster(Sa + (unsigned)(off * 8), sy < 0 ? down : up);
+        }
+      }
+      const double qx = Q[l], qy = Q[L + l];
+      if (KIND == 0) {
+        if (last_mon) {
+          if (ARITH == 0 || !collide_fix<true, false, true>(f, qx, qy, c0.fx, o, m1, m2))
+            collide<false>(f, qx, qy, c0, o, m1, m2);
+        } else if (ARITH == 0 || !collide_fix<false, false, true>(f, qx, qy, c0.fx, o, m1, m2)) {
+          collide<false>(f, qx, qy, c0, o, m1, m2);
+        }
+      } else {
+        if (last_mon) {
+          if (ARITH == 0 || !collide_T_fix<true, false, false, true>(f, qx, qy, c0.fx, o, m1, m2))
+            collide_T<false>(f, qx, qy, c0, o, m1, m2);
+        } else if (ARITH == 0 ||
+                   !collide_T_fix<false, false, false, true>(f, qx, qy, c0.fx, o, m1, m2)) {
+          collide_T<false>(f, qx, qy, c0, o, m1, m2);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) D[k * L + l] = o[k];
+      if (last_mon) mon[0] += m1 * m1 + m2 * m2;
+    }
+    cluster_sync_release_acquire();
+  }
+  if (nsweeps > 0) {
+    const double *fin = (nsweeps & 1) ? B1 : B0, *prev = (nsweeps & 1) ? B0 : B1;
+    double *gfin = (nsweeps & 1) ? b2 : a, *gprev = (nsweeps & 1) ? a : b2;
+    for (long l = threadIdx.x; l < L; l += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        gfin[k * g.N + base + l] = fin[k * L + l];
+        gprev[k * g.N + base + l] = prev[k * L + l];
+      }
+    }
+  }
+  if (monitor) {
+    __shared__ double sm[32];
+    block_sum<1>(mon, sm);
+    if (threadIdx.x == 0) partial[rank] = mon[0];
+    if (rank == 0)
+      for (long i = (long)C + threadIdx.x; i < npartial; i += blockDim.x) partial[i] = 0.0;
+  }
+}
+
 // Residual partials: max |a - b| and max |a| over all planes.
 static __global__ void __launch_bounds__(256) k_residual(const double *__restrict__ a,
                                                   const double *__restrict__ bb, long total,

@@ -57,6 +57,9 @@ struct lbm_solid {
   // cluster-resident sweeps of small periodic lattices (0 CTAs: not used)
   ClusterWork cw{};
   int cl_ncta = 0, cl_threads = 0;
+  // lattice resident in distributed shared memory (0 CTAs: not used)
+  int dsm_ncta = 0, dsm_h = 0, dsm_threads = 0;
+  size_t dsm_smem = 0;
   Field fl{};
   bool field = false;
   // CUDA graphs of sweep chunks (launch overhead dominates small lattices): captured on
@@ -324,6 +327,92 @@ int compact_block_size(long nb, long nchunk) {
 }
 bool compact_hoist(long nb, long nchunk) { return compact_block_size(nb, nchunk) == 32; }
 
+// ---- lattices resident in distributed shared memory (k_sweeps_dsm) -------------------
+// Measured on B300 (us per sweep, graph-replayed / L2 cluster / distributed shared
+// memory): 16^2 2.19 / 1.61 / 1.72, 32^2 2.20 / 1.63 / 1.69, 40^2 2.22 / 1.73 / 2.10,
+// 64^2 2.24 / 2.50 / 2.06, 80^2 2.25 / 3.34 / 3.14, 128^2 2.31 / 5.79 / 5.79.  A sweep of
+// a cluster-resident lattice costs one warp's collisions plus the cluster barrier, and
+// the L2 round trip the shared-memory lattice saves is a small part of it; one GPC's 16
+// SMs fall behind the whole GPU from ~80^2.  So: the L2 cluster up to 2048 nodes, the
+// shared-memory lattice above that up to 4096 nodes (64^2: time to gradient 5.36 -> 5.05
+// ms), graph-replayed launches beyond.
+constexpr long kDsmMaxNodes = 4096;
+constexpr long kDsmBandNodes = 128;
+
+template <int KIND, int ARITH>
+cudaError_t launch_dsm(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
+                       int *fits = nullptr) {
+  auto kern = k_sweeps_dsm<KIND, ARITH>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)h->dsm_ncta);
+  cfg.blockDim = dim3((unsigned)h->dsm_threads);
+  cfg.dynamicSmemBytes = h->dsm_smem;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)h->dsm_ncta;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (probe) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dsm_smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveClusters(fits, kern, &cfg);
+  }
+  double *a = KIND == 0 ? h->fcur : h->pcur, *b = KIND == 0 ? h->fnext : h->pnext;
+  const double *src = KIND == 0 ? h->g2 : h->r2;
+  return cudaLaunchKernelEx(&cfg, kern, a, b, src, h->grid, h->coef, h->dsm_h, nsweeps,
+                            monitor ? 1 : 0, h->partial, h->nmon);
+}
+
+template <int KIND>
+cudaError_t launch_dsm_any(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
+                           int *fits = nullptr) {
+  return h->kernel == LBM_KERNEL_FP64 ? launch_dsm<KIND, 0>(h, nsweeps, monitor, probe, fits)
+                                      : launch_dsm<KIND, 1>(h, nsweeps, monitor, probe, fits);
+}
+
+// Chooses the cluster for a lattice held in distributed shared memory: C CTAs with C
+// dividing ny (bands of whole rows), at most one GPC's worth, the fewest CTAs whose band
+// holds at most 128 nodes (one warp per SM sub-partition: a sweep is the latency of one
+// warp's collisions plus the barrier) when there is one, else the most that fit; checks
+// that such a cluster can be scheduled with its shared memory.
+void setup_dsm(lbm_solid *h) {
+  h->dsm_ncta = 0;
+  if (!h->periodic || h->field || h->N <= kClusterMaxItems || h->N > kDsmMaxNodes) return;
+  int dev = 0, smem_max = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess)
+    return;
+  smem_max -= 1024;  // the kernel's static reduction scratch
+  std::vector<int> order;
+  for (int c = 1; c <= kClusterMaxCta; ++c)
+    if (h->ny % c == 0 && (long)(h->ny / c) * h->nx <= kDsmBandNodes) order.push_back(c);
+  for (int c = kClusterMaxCta; c >= 1; --c)
+    if (h->ny % c == 0 && (long)(h->ny / c) * h->nx > kDsmBandNodes) order.push_back(c);
+  for (int c : order) {
+    const long L = (long)(h->ny / c) * h->nx;
+    const size_t bytes = (size_t)L * kDsmDoublesPerNode * sizeof(double);
+    if (bytes > (size_t)smem_max) continue;
+    h->dsm_ncta = c;
+    h->dsm_h = h->ny / c;
+    h->dsm_threads = (int)std::min<long>(1024, (L + 31) / 32 * 32);
+    h->dsm_smem = bytes;
+    int f0 = 0, f1 = 0;
+    if (launch_dsm_any<0>(h, 0, false, true, &f0) == cudaSuccess && f0 > 0 &&
+        launch_dsm_any<1>(h, 0, false, true, &f1) == cudaSuccess && f1 > 0) {
+      if (h->nmon < c) h->nmon = c;
+      return;
+    }
+    cudaGetLastError();  // clear a refused configuration, try the next
+  }
+  h->dsm_ncta = 0;
+}
+
 // Chooses the cluster shape for a small lattice (CTAs of whole warps, about one item per
 // thread, as many CTAs as a GPC allows) and checks that such a cluster can be scheduled;
 // otherwise the handle keeps the graph-replayed launches.
@@ -467,12 +556,15 @@ lbm_status run_sweeps(lbm_solid *h, int kind, long k, bool mon) {
     h->pcur_rest = false;
     --k;
   }
-  if (h->cl_ncta > 0) {  // small lattice: cluster-resident launches of up to 512 sweeps
+  if (h->dsm_ncta > 0 || h->cl_ncta > 0) {  // small lattice: cluster launches of <= 512 sweeps
+    const bool dsm = h->dsm_ncta > 0;
     while (k > 0) {
       const long c = k > kClusterChunk ? kClusterChunk : k;
       const bool m = mon && c == k;
-      const cudaError_t e = kind == 0 ? launch_cluster_any<0>(h, (int)c, m)
-                                      : launch_cluster_any<1>(h, (int)c, m);
+      const cudaError_t e =
+          dsm ? (kind == 0 ? launch_dsm_any<0>(h, (int)c, m) : launch_dsm_any<1>(h, (int)c, m))
+              : (kind == 0 ? launch_cluster_any<0>(h, (int)c, m)
+                           : launch_cluster_any<1>(h, (int)c, m));
       if (e != cudaSuccess)
         return fail(h, LBM_ERR_CUDA, std::string("cluster launch: ") + cudaGetErrorString(e));
       LAUNCHED(h);
@@ -898,6 +990,7 @@ lbm_status lbm_solid_create(const lbm_solid_desc *d, void *stream, lbm_solid **o
   if (h->periodic) {
     h->cw = ClusterWork{nullptr, N};
     setup_cluster(h, N);
+    if (h->cl_ncta == 0) setup_dsm(h);
   }
   *out = h;
   return LBM_OK;

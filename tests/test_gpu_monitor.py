@@ -74,8 +74,10 @@ def plate_case(Nx):
     return g, F * geo.active, dstar, I.PLATE_E, extra
 
 
+# 16^2 and 32^2 run cluster launches through L2, 48^2 the lattice held in distributed
+# shared memory, the plate graph-replayed compact launches
 CASES = [("periodic", 16, 16, 30, 1e-6), ("periodic", 32, 64, 30, 1e-6),
-         ("plate", 10, 16, 25, 1e-4)]
+         ("periodic", 48, 64, 30, 1e-6), ("plate", 10, 16, 25, 1e-4)]
 
 
 def make(lbm_mod, g, E, extra, kernel):

@@ -38,9 +38,14 @@ def lbm_mod():
     return lbm
 
 
-# (nx, ny, E, nu, steps): tiny wraps, ragged tiles, several blocks in x and y
+# (nx, ny, E, nu, steps): tiny wraps, ragged tiles, several blocks in x and y.  Up to
+# 2048 nodes the sweeps run as cluster launches through L2, from 2049 to 4096 nodes as a
+# lattice held in distributed shared memory (257 x 9: bands of one row, both neighbour
+# rows remote; 64^2 with an odd count of 601 sweeps: two launches; 50 x 45: a cluster
+# of 15 CTAs), above that as graph-replayed launches.
 CASES = [(3, 3, 1.0, 0.3, 7), (4, 5, 0.11, 0.8, 20), (7, 3, 0.5, -0.2, 13),
-         (33, 17, 0.11, 0.8, 40), (130, 67, 2.0, 0.25, 25), (257, 9, 0.7, 0.1, 11)]
+         (33, 17, 0.11, 0.8, 40), (130, 67, 2.0, 0.25, 25), (257, 9, 0.7, 0.1, 11),
+         (64, 64, 1.0, 0.3, 601), (50, 45, 0.11, 0.8, 40)]
 
 
 def periodic_problem(nx, ny, seed):
