@@ -1117,6 +1117,65 @@ __device__ __forceinline__ unsigned cluster_size() {
   return r;
 }
 
+// State of a solve loop that runs on the device (a cluster kernel that loops over chunks
+// itself, or a CUDA graph whose conditional WHILE node repeats chunk -> residual ->
+// decision): the tolerance and the chunk limit in, the chunks run and the last residual
+// out.
+struct LoopState {
+  double tol;
+  long long max_iters, iters;
+  double metric;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ double ld_cluster(unsigned local_addr, unsigned rank) {
+  unsigned remote;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+// The residual rule's decision at the end of a chunk, taken identically by every CTA of
+// a cluster: (v0, v1) are the thread's max |f(t) - f(t-1)| and max |f(t)|; the cluster
+// maxima (NaN propagating, so order-free) give r = v0 / v1, as the host loop computes it;
+// stop when r is below tol or not finite, or when chunk `it` is the last allowed.
+// `red` (2 doubles) and `flag` are the CTA's shared slots, `sm` block_max scratch.
+__device__ __forceinline__ bool cluster_residual_stop(double v0, double v1, double tol,
+                                                      long long it, long long max_iters,
+                                                      double *red, double *sm, double *flag) {
+  double v[2] = {v0, v1};
+  block_max<2>(v, sm);
+  if (threadIdx.x == 0) {
+    red[0] = v[0];
+    red[1] = v[1];
+  }
+  cluster_sync_release_acquire();
+  if (threadIdx.x < 32) {  // lane q reads CTA q's maxima (a cluster has at most 16 CTAs)
+    const unsigned C = cluster_size(), q = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (q < C) {
+      a = ld_cluster(smem_addr(red), q);
+      b = ld_cluster(smem_addr(red + 1), q);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a = nan_max(a, __shfl_down_sync(0xffffffffu, a, o));
+      b = nan_max(b, __shfl_down_sync(0xffffffffu, b, o));
+    }
+    if (q == 0) {
+      double r = b > 0.0 ? a / b : (a > 0.0 ? INFINITY : 0.0);
+      if (!isfinite(a) || !isfinite(b)) r = NAN;
+      flag[0] = (!(r >= tol) || it + 1 >= max_iters) ? 1.0 : 0.0;
+      flag[1] = r;
+    }
+  }
+  __syncthreads();
+  return flag[0] != 0.0;
+}
+
 // One item of a primal sweep (coherent population loads); mon += |d|^2 if MON.
 template <bool BOUNDED, int ARITH, bool FIELD, bool MON>
 __device__ __forceinline__ void primal_item(const double *fin, double *fout,
@@ -1197,17 +1256,59 @@ __device__ __forceinline__ void adjoint_item(const double *pin, double *pout,
 // (b after an odd count).  With monitor, the last sweep's partial sums of |d|^2 go to
 // partial[rank] and partial[ncta .. npartial) are zeroed, so the usual finishing pass
 // over npartial entries gives the monitor.  Launched as ONE cluster of gridDim.x CTAs.
+// With chunk > 0 (even) the kernel is the whole residual-rule solve loop instead: chunks
+// of `chunk` sweeps, each followed by the residual of its last two states and the
+// cluster-wide decision (cluster_residual_stop), at most max_iters chunks; ls receives
+// the chunks run and the last residual.
 template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
-__global__ void __launch_bounds__(512) k_sweeps_cl(double *a, double *b2,
+__global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
                                                     const double *__restrict__ src2, Grid g,
                                                     Bounded b, Compact c, Coef c0, Field fl,
                                                     ClusterWork w, int nsweeps, int monitor,
                                                     double *__restrict__ partial,
-                                                    long npartial) {
+                                                    long npartial, int chunk,
+                                                    long long max_iters, double tol,
+                                                    LoopState *ls) {
   const unsigned rank = cluster_rank(), ncta = cluster_size();
   const long T = (long)ncta * blockDim.x;
   const long t0 = (long)rank * blockDim.x + threadIdx.x;
   double mon[1] = {0.0};
+  if (chunk > 0) {
+    __shared__ double red[2], flag[2], smx[64];
+    for (long long it = 0;; ++it) {
+      for (int s = 0; s < chunk; ++s) {
+        const double *in = (s & 1) ? b2 : a;
+        double *out = (s & 1) ? a : b2;
+        for (long i = t0; i < w.nitems; i += T) {
+          if (KIND == 0)
+            primal_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, i, mon[0]);
+          else
+            adjoint_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, i, mon[0]);
+        }
+        cluster_sync_release_acquire();
+      }
+      // an even chunk leaves the latest state in a, the one before it in b2
+      double v0 = 0.0, v1 = 0.0;
+      for (long i = t0; i < w.nitems; i += T) {
+        const long n = !BOUNDED ? i : (i < c.nb ? (long)c.bnode[i] : (long)w.inner[i - c.nb]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const double ai = a[k * g.N + n];
+          v0 = nan_max(v0, fabs(ai - b2[k * g.N + n]));
+          v1 = nan_max(v1, fabs(ai));
+        }
+      }
+      if (cluster_residual_stop(v0, v1, tol, it, max_iters, red, smx, flag)) {
+        if (rank == 0 && threadIdx.x == 0) {
+          ls->iters = it + 1;
+          ls->metric = flag[1];
+        }
+        break;
+      }
+    }
+    cluster_sync_release_acquire();  // no CTA leaves while another may read its `red`
+    return;
+  }
   for (int s = 0; s < nsweeps; ++s) {
     const double *in = (s & 1) ? b2 : a;
     double *out = (s & 1) ? a : b2;
@@ -1250,27 +1351,19 @@ __global__ void __launch_bounds__(512) k_sweeps_cl(double *a, double *b2,
 // as the graph-replayed sweeps leave them.  Populations are converted on the integer
 // pipes (a CTA holds few warps, and a lone warp's FP64 instruction costs 64 cycles).
 
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ double ld_cluster(unsigned local_addr, unsigned rank) {
-  unsigned remote;
-  double v;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
-  return v;
-}
-
 // Dynamic shared memory of k_sweeps_dsm: 18 doubles per node of the band.
 constexpr int kDsmDoublesPerNode = 18;
 
+// With chunk > 0 (even): the residual-rule solve loop as in k_sweeps_cl, the residual
+// read from the two shared-memory buffers.
 template <int KIND, int ARITH>
-__global__ void __launch_bounds__(1024) k_sweeps_dsm(double *a, double *b2,
+__global__ void __launch_bounds__(512) k_sweeps_dsm(double *a, double *b2,
                                                      const double *__restrict__ src2, Grid g,
                                                      Coef c0, int h, int nsweeps, int monitor,
                                                      double *__restrict__ partial,
-                                                     long npartial) {
+                                                     long npartial, int chunk,
+                                                     long long max_iters, double tol,
+                                                     LoopState *ls) {
   extern __shared__ __align__(16) double dsm[];
   const unsigned rank = cluster_rank(), C = cluster_size();
   const int nx = g.nx;
@@ -1285,12 +1378,36 @@ __global__ void __launch_bounds__(1024) k_sweeps_dsm(double *a, double *b2,
   }
   const unsigned up = (rank + 1) % C, down = (rank + C - 1) % C;
   double mon[1] = {0.0};
+  __shared__ double red[2], flag[2], smx[64];
   cluster_sync_release_acquire();
-  for (int s = 0; s < nsweeps; ++s) {
+  long long it = 0;
+  const int per = chunk > 0 ? chunk : nsweeps;
+  for (int s = 0;; ++s) {
+    if (s == per) {  // end of a chunk (loop mode) or of the run
+      if (chunk <= 0) break;
+      double v0 = 0.0, v1 = 0.0;  // an even chunk: latest state in B0, the one before in B1
+      for (long l = threadIdx.x; l < L; l += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const double ai = B0[k * L + l];
+          v0 = nan_max(v0, fabs(ai - B1[k * L + l]));
+          v1 = nan_max(v1, fabs(ai));
+        }
+      }
+      if (cluster_residual_stop(v0, v1, tol, it, max_iters, red, smx, flag)) {
+        if (rank == 0 && threadIdx.x == 0) {
+          ls->iters = it + 1;
+          ls->metric = flag[1];
+        }
+        break;
+      }
+      ++it;
+      s = 0;
+    }
     const double *S = (s & 1) ? B1 : B0;
     double *D = (s & 1) ? B0 : B1;
     const unsigned Sa = smem_addr(S);
-    const bool last_mon = monitor && s == nsweeps - 1;
+    const bool last_mon = chunk <= 0 && monitor && s == nsweeps - 1;
     for (long l = threadIdx.x; l < L; l += blockDim.x) {
       const int x = (int)(l % nx), yl = (int)(l / nx);
       // source of link k: primal pulls from x - c_k, the adjoint from x + c_k; rows
@@ -1332,9 +1449,10 @@ __global__ void __launch_bounds__(1024) k_sweeps_dsm(double *a, double *b2,
     }
     cluster_sync_release_acquire();
   }
-  if (nsweeps > 0) {
-    const double *fin = (nsweeps & 1) ? B1 : B0, *prev = (nsweeps & 1) ? B0 : B1;
-    double *gfin = (nsweeps & 1) ? b2 : a, *gprev = (nsweeps & 1) ? a : b2;
+  if (per > 0) {
+    const bool odd = chunk <= 0 && (nsweeps & 1);
+    const double *fin = odd ? B1 : B0, *prev = odd ? B0 : B1;
+    double *gfin = odd ? b2 : a, *gprev = odd ? a : b2;
     for (long l = threadIdx.x; l < L; l += blockDim.x) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
@@ -1343,6 +1461,7 @@ __global__ void __launch_bounds__(1024) k_sweeps_dsm(double *a, double *b2,
       }
     }
   }
+  if (chunk > 0) cluster_sync_release_acquire();  // no CTA leaves while another reads `red`
   if (monitor) {
     __shared__ double sm[32];
     block_sum<1>(mon, sm);
@@ -1350,6 +1469,21 @@ __global__ void __launch_bounds__(1024) k_sweeps_dsm(double *a, double *b2,
     if (rank == 0)
       for (long i = (long)C + threadIdx.x; i < npartial; i += blockDim.x) partial[i] = 0.0;
   }
+}
+
+// The decision at the end of a chunk, from the reduced residual partials (max |a - b|,
+// max |a|): the same relative residual as the host loop computes, stop (condition 0)
+// when it is below tol, not finite, or the chunk limit is reached.
+static __global__ void k_loop_decide(const double *__restrict__ dres, LoopState *ls,
+                                     cudaGraphConditionalHandle hnd) {
+  const double a = dres[0], b = dres[1];
+  double r = b > 0.0 ? a / b : (a > 0.0 ? INFINITY : 0.0);
+  if (!isfinite(a) || !isfinite(b)) r = NAN;
+  const long long it = ls->iters + 1;
+  ls->iters = it;
+  ls->metric = r;
+  const bool stop = !(r >= ls->tol) || it >= ls->max_iters;
+  cudaGraphSetConditional(hnd, stop ? 0u : 1u);
 }
 
 // Residual partials: max |a - b| and max |a| over all planes.

@@ -72,6 +72,12 @@ struct lbm_solid {
     cudaGraphExec_t exec;
   };
   std::vector<GraphEnt> graphs;
+  // device-side solve loops (residual rule): graphs with a conditional WHILE node over
+  // chunks of c sweeps, keyed like the sweep graphs; their state block in device and
+  // pinned host memory
+  std::vector<GraphEnt> loops;
+  LoopState *dloop = nullptr, *hloop = nullptr;
+  bool no_dloop = false;  // a loop graph could not be built: host loop only
   long version = 0;
   // forward-mode tangent (f-AD) buffers, allocated on first use
   double *tA = nullptr, *tB = nullptr, *qdot = nullptr;
@@ -277,7 +283,8 @@ constexpr long kClusterChunk = 512;           // sweeps per launch (fixed-step r
 
 template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
 cudaError_t launch_cluster(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
-                           int *fits = nullptr) {
+                           int *fits = nullptr, int chunk = 0, long long max_iters = 0,
+                           double tol = 0.0) {
   auto kern = k_sweeps_cl<KIND, BOUNDED, ARITH, FIELD>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h->cl_ncta);
@@ -298,19 +305,21 @@ cudaError_t launch_cluster(lbm_solid *h, int nsweeps, bool monitor, bool probe =
   double *a = KIND == 0 ? h->fcur : h->pcur, *b = KIND == 0 ? h->fnext : h->pnext;
   const double *src = KIND == 0 ? h->g2 : h->r2;
   return cudaLaunchKernelEx(&cfg, kern, a, b, src, h->grid, h->bnd, h->cmp, h->coef, h->fl,
-                            h->cw, nsweeps, monitor ? 1 : 0, h->partial, h->nmon);
+                            h->cw, nsweeps, monitor ? 1 : 0, h->partial, h->nmon, chunk,
+                            max_iters, tol, h->dloop);
 }
 
 // (periodic lattices only: bounded grids measured no gain, see kClusterMaxItems)
 template <int KIND>
 cudaError_t launch_cluster_any(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
-                               int *fits = nullptr) {
+                               int *fits = nullptr, int chunk = 0, long long max_iters = 0,
+                               double tol = 0.0) {
   const bool fp = h->kernel == LBM_KERNEL_FP64;
   if (h->field)
-    return fp ? launch_cluster<KIND, false, 0, true>(h, nsweeps, monitor, probe, fits)
-              : launch_cluster<KIND, false, 1, true>(h, nsweeps, monitor, probe, fits);
-  return fp ? launch_cluster<KIND, false, 0, false>(h, nsweeps, monitor, probe, fits)
-            : launch_cluster<KIND, false, 1, false>(h, nsweeps, monitor, probe, fits);
+    return fp ? launch_cluster<KIND, false, 0, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol)
+              : launch_cluster<KIND, false, 1, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol);
+  return fp ? launch_cluster<KIND, false, 0, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol)
+            : launch_cluster<KIND, false, 1, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol);
 }
 
 // Launch shape of the compact sweep of a bounded grid.  Below ~32 warps per SM the sweep
@@ -341,7 +350,8 @@ constexpr long kDsmBandNodes = 128;
 
 template <int KIND, int ARITH>
 cudaError_t launch_dsm(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
-                       int *fits = nullptr) {
+                       int *fits = nullptr, int chunk = 0, long long max_iters = 0,
+                       double tol = 0.0) {
   auto kern = k_sweeps_dsm<KIND, ARITH>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h->dsm_ncta);
@@ -365,14 +375,17 @@ cudaError_t launch_dsm(lbm_solid *h, int nsweeps, bool monitor, bool probe = fal
   double *a = KIND == 0 ? h->fcur : h->pcur, *b = KIND == 0 ? h->fnext : h->pnext;
   const double *src = KIND == 0 ? h->g2 : h->r2;
   return cudaLaunchKernelEx(&cfg, kern, a, b, src, h->grid, h->coef, h->dsm_h, nsweeps,
-                            monitor ? 1 : 0, h->partial, h->nmon);
+                            monitor ? 1 : 0, h->partial, h->nmon, chunk, max_iters, tol,
+                            h->dloop);
 }
 
 template <int KIND>
 cudaError_t launch_dsm_any(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
-                           int *fits = nullptr) {
-  return h->kernel == LBM_KERNEL_FP64 ? launch_dsm<KIND, 0>(h, nsweeps, monitor, probe, fits)
-                                      : launch_dsm<KIND, 1>(h, nsweeps, monitor, probe, fits);
+                           int *fits = nullptr, int chunk = 0, long long max_iters = 0,
+                           double tol = 0.0) {
+  return h->kernel == LBM_KERNEL_FP64
+             ? launch_dsm<KIND, 0>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol)
+             : launch_dsm<KIND, 1>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol);
 }
 
 // Chooses the cluster for a lattice held in distributed shared memory: C CTAs with C
@@ -400,7 +413,7 @@ void setup_dsm(lbm_solid *h) {
     if (bytes > (size_t)smem_max) continue;
     h->dsm_ncta = c;
     h->dsm_h = h->ny / c;
-    h->dsm_threads = (int)std::min<long>(1024, (L + 31) / 32 * 32);
+    h->dsm_threads = (int)std::min<long>(512, (L + 31) / 32 * 32);
     h->dsm_smem = bytes;
     int f0 = 0, f1 = 0;
     if (launch_dsm_any<0>(h, 0, false, true, &f0) == cudaSuccess && f0 > 0 &&
@@ -422,7 +435,7 @@ void setup_cluster(lbm_solid *h, long items) {
   for (int ncta = (int)std::min<long>(kClusterMaxCta, (items + 31) / 32); ncta >= 1; ncta /= 2) {
     const long per = (items + ncta - 1) / ncta;
     h->cl_ncta = ncta;
-    h->cl_threads = (int)std::min<long>(512, (per + 31) / 32 * 32);
+    h->cl_threads = (int)std::min<long>(256, (per + 31) / 32 * 32);
     int f0 = 0, f1 = 0;
     if (launch_cluster_any<0>(h, 0, false, true, &f0) == cudaSuccess && f0 > 0 &&
         launch_cluster_any<1>(h, 0, false, true, &f1) == cudaSuccess && f1 > 0) {
@@ -627,6 +640,139 @@ lbm_status residual(lbm_solid *h, const double *a, const double *b, double &res)
   return LBM_OK;
 }
 
+// The device-side solve loop for the residual rule: a graph whose conditional WHILE node
+// runs [c sweeps (c even, so the buffers return to the same roles), residual partials,
+// their reduction, k_loop_decide] until the residual is below tol, not finite, or the
+// chunk limit in the state block is reached.  No host round trip per chunk.
+lbm_status loop_graph_for(lbm_solid *h, int kind, long c, cudaGraphExec_t &exec) {
+  const int parity = kind == 0 ? (h->fcur == h->fA ? 0 : 1) : (h->pcur == h->pA ? 0 : 1);
+  for (const auto &g : h->loops)
+    if (g.kind == kind && g.k == c && g.parity == parity && g.version == h->version) {
+      exec = g.exec;
+      return LBM_OK;
+    }
+  if (!h->cap) CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  CK(h, cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle hnd;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&hnd, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(h->cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(h, LBM_ERR_CUDA, std::string("loop graph: ") + cudaGetErrorString(e));
+  }
+  double *f0 = h->fcur, *f1 = h->fnext, *p0 = h->pcur, *p1 = h->pnext;
+  cudaStream_t user = h->stream;
+  h->stream = h->cap;
+  cudaError_t el = cudaSuccess;
+  if (h->dsm_ncta > 0 || h->cl_ncta > 0) {  // one cluster launch of c sweeps
+    el = h->dsm_ncta > 0
+             ? (kind == 0 ? launch_dsm_any<0>(h, (int)c, false) : launch_dsm_any<1>(h, (int)c, false))
+             : (kind == 0 ? launch_cluster_any<0>(h, (int)c, false)
+                          : launch_cluster_any<1>(h, (int)c, false));
+  } else {
+    for (long i = 0; i < c; ++i) {
+      if (kind == 0) {
+        launch_primal_any(h, false);
+        std::swap(h->fcur, h->fnext);
+      } else {
+        launch_adjoint_any(h, false);
+        std::swap(h->pcur, h->pnext);
+      }
+    }
+  }
+  // residual of the chunk's last two states (as residual(), without the fetch)
+  const double *ra = kind == 0 ? f0 : p0, *rb = kind == 0 ? f1 : p1;
+  long blocks;
+  if (h->periodic) {
+    const long total = 8 * h->N;
+    blocks = (total + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    k_residual<<<(unsigned)blocks, 256, 0, h->stream>>>(ra, rb, total, h->partial);
+  } else {
+    blocks = h->cblocks;
+    k_residual_c<<<(unsigned)blocks, h->ctpb, 0, h->stream>>>(ra, rb, h->grid, h->cmp, h->partial);
+  }
+  k_finish<<<1, 256, 0, h->stream>>>(h->partial, blocks, 2, 1, 1.0, h->dres);
+  k_loop_decide<<<1, 1, 0, h->stream>>>(h->dres, h->dloop, hnd);
+  cudaGraph_t body = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(h->cap, &body);
+  h->stream = user;
+  h->fcur = f0; h->fnext = f1; h->pcur = p0; h->pnext = p1;
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t ei = (el == cudaSuccess && ec == cudaSuccess) ? cudaGraphInstantiate(&ex, graph, 0)
+                                                             : (el != cudaSuccess ? el : ec);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, LBM_ERR_CUDA, std::string("loop graph: ") + cudaGetErrorString(ei));
+  }
+  if (h->loops.size() >= 8) {
+    cudaGraphExecDestroy(h->loops.front().exec);
+    h->loops.erase(h->loops.begin());
+  }
+  h->loops.push_back(lbm_solid::GraphEnt{kind, parity, 0, c, h->version, ex});
+  exec = ex;
+  return LBM_OK;
+}
+
+// Runs up to max_iters chunks of c sweeps on the device (residual rule); returns the
+// chunks run and the last residual.  ok = false when no loop graph can be built (the
+// caller keeps the host loop).
+lbm_status device_loop(lbm_solid *h, int kind, long c, long max_iters, double tol,
+                       long &iters, double &metric, bool &ok) {
+  ok = false;
+  if (h->no_dloop) return LBM_OK;
+  if (!h->dloop) {
+    CK(h, cudaMalloc((void **)&h->dloop, sizeof(LoopState)));
+    CK(h, cudaMallocHost((void **)&h->hloop, sizeof(LoopState)));
+  }
+  *h->hloop = LoopState{tol, max_iters, 0, 0.0};
+  if (h->dsm_ncta > 0 || h->cl_ncta > 0) {
+    // a cluster-resident lattice: the kernel itself loops over the chunks
+    if (c > INT32_MAX) return LBM_OK;
+    CK(h, cudaMemcpyAsync(h->dloop, h->hloop, sizeof(LoopState), cudaMemcpyHostToDevice, h->stream));
+    const cudaError_t e =
+        h->dsm_ncta > 0
+            ? (kind == 0 ? launch_dsm_any<0>(h, 0, false, false, nullptr, (int)c, max_iters, tol)
+                         : launch_dsm_any<1>(h, 0, false, false, nullptr, (int)c, max_iters, tol))
+            : (kind == 0 ? launch_cluster_any<0>(h, 0, false, false, nullptr, (int)c, max_iters, tol)
+                         : launch_cluster_any<1>(h, 0, false, false, nullptr, (int)c, max_iters, tol));
+    if (e != cudaSuccess)
+      return fail(h, LBM_ERR_CUDA, std::string("cluster loop launch: ") + cudaGetErrorString(e));
+    ++h->launches;
+  } else {
+    cudaGraphExec_t ex = nullptr;
+    if (loop_graph_for(h, kind, c, ex) != LBM_OK) {
+      h->no_dloop = true;  // e.g. a launch form that capture into a conditional body refuses
+      h->err.clear();
+      return LBM_OK;
+    }
+    CK(h, cudaMemcpyAsync(h->dloop, h->hloop, sizeof(LoopState), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaGraphLaunch(ex, h->stream));
+  }
+  CK(h, cudaMemcpyAsync(h->hloop, h->dloop, sizeof(LoopState), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  iters = (long)h->hloop->iters;
+  metric = h->hloop->metric;
+  if (!(h->dsm_ncta > 0 || h->cl_ncta > 0)) h->launches += iters * (c + 3);
+  if (kind == 0) ++h->pstate;
+  ok = true;
+  return LBM_OK;
+}
+
 // Shared stopping loop of the primal and adjoint solves.
 template <class Resid>
 lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *info, int kind,
@@ -676,7 +822,22 @@ lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *inf
         if (st) return st;
         metric = v;
         if (std::isnan(v)) { result = LBM_ERR_DIVERGED; break; }
-        if (v < o->tol) done = true;
+        if (v < o->tol) { done = true; break; }
+        // the remaining whole chunks on the device (the first chunk, which may hold the
+        // collide-only or from-rest first sweep, ran above)
+        const long c = o->check_every, iters_max = (o->max_steps - steps) / c;
+        if (c % 2 == 0 && iters_max >= 1) {
+          long iters = 0;
+          double mv = 0.0;
+          bool ok = false;
+          if ((st = device_loop(h, kind, c, iters_max, o->tol, iters, mv, ok))) return st;
+          if (ok) {
+            steps += iters * c;
+            metric = mv;
+            if (std::isnan(mv)) { result = LBM_ERR_DIVERGED; break; }
+            if (mv < o->tol) { done = true; break; }
+          }
+        }
       }
     }
     if (result == LBM_OK && !done) result = LBM_ERR_NOT_CONVERGED;
@@ -1001,7 +1162,11 @@ lbm_status lbm_solid_destroy(lbm_solid *h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
+  for (auto &g : h->loops) cudaGraphExecDestroy(g.exec);
+  h->loops.clear();
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->dloop) cudaFree(h->dloop);
+  if (h->hloop) cudaFreeHost(h->hloop);
   free_all(h);
   delete h;
   return LBM_OK;
