@@ -406,6 +406,127 @@ __global__ void __launch_bounds__(256) k_grad_force(const double *__restrict__ p
   }
 }
 
+// ---------------------------------------------------------------------------------
+// The objective pass and the force gradient of a periodic lattice with the node's
+// arithmetic on the integer pipes.  Both kernels move ~100 B per node and did ~20 FP64
+// instructions per node, which held them at ~2 TB/s on B300's FP64 pipe; here the
+// differences of populations, force and target are formed in 64-bit fixed point at the
+// largest exponent of the node's inputs (exact sums of the truncated inputs, one rounding
+// back to binary64, within a few 2^-56 of the node's largest input, like the sweeps), and
+// only the products and the sums of the reduction stay in FP64.  Nodes whose inputs fall
+// outside [kEmin, kEmax] use the FP64 formula.  Grid-stride over the nodes (a fixed grid,
+// so the partials and their reduction order are fixed).
+
+// largest biased exponent of n values
+template <int NV>
+__device__ __forceinline__ int max_exp_n(const double (&v)[NV]) {
+  int m = 0;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) m = max(m, __double2hiint(v[i]) & 0x7fffffff);
+  return m >> 20;
+}
+
+// e = d - d* (Eq. node_J) of one node from its pulled populations, force and target.
+__device__ __forceinline__ void residual_e(const double (&f)[8], double gx, double gy,
+                                           double sx, double sy, double &ex, double &ey) {
+  const double v[12] = {f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], gx, gy, sx, sy};
+  const int E = max_exp_n<12>(v);
+  if (E >= kEmin && E <= kEmax) {
+    long long F[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) F[k] = to_fix_alu(f[k], E);
+    const long long b3 = F[4] - F[6], b4 = F[5] - F[7];
+    const long long EX = (F[0] - F[2]) + (b3 - b4) + 2 * to_fix_alu(gx, E) - to_fix_alu(sx, E);
+    const long long EY = (F[1] - F[3]) + (b3 + b4) + 2 * to_fix_alu(gy, E) - to_fix_alu(sy, E);
+    ex = from_fix(EX, E);
+    ey = from_fix(EY, E);
+  } else {
+    ex = (f[0] - f[2]) + (f[4] - f[6]) - (f[5] - f[7]) + 2.0 * gx - sx;
+    ey = (f[1] - f[3]) + (f[4] - f[6]) + (f[5] - f[7]) + 2.0 * gy - sy;
+  }
+}
+
+template <bool OBS>
+__global__ void __launch_bounds__(256) k_objective_fix(const double *__restrict__ src,
+                                                       const double *__restrict__ g2,
+                                                       const double *__restrict__ dstar,
+                                                       const double *__restrict__ obs,
+                                                       double *__restrict__ r, double scale,
+                                                       Grid g, double *__restrict__ partial) {
+  double acc[1] = {0.0};
+  const Bounded none{};
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < g.N;
+       n += (long)gridDim.x * blockDim.x) {
+    const int y = (int)(n / g.nx), x = (int)(n - (long)y * g.nx);
+    double f[8], gsel, ex, ey;
+    pull_primal<false>(src, x, y, g, none, f, gsel);
+    residual_e(f, __ldg(g2 + n), __ldg(g2 + g.N + n), __ldg(dstar + n), __ldg(dstar + g.N + n),
+               ex, ey);
+    const double w = OBS ? __ldg(obs + n) : 1.0;
+    const double e2 = fma(ex, ex, ey * ey);
+    acc[0] += OBS ? w * e2 : e2;
+    const double sw = OBS ? scale * w : scale;
+    r[n] = sw * ex;
+    r[g.N + n] = sw * ey;
+  }
+  __shared__ double sm[32];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+}
+
+// Eq. optimality as k_grad_force: dJ/dF_n = dx^2 (r_n / 2 - (dC/dg)^T phi_S,n); MODE 0
+// the field (and its component sums), MODE 1 the two basis projections.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_grad_force_fix(const double *__restrict__ pin,
+                                                        const double *__restrict__ r,
+                                                        const double *__restrict__ basis,
+                                                        double *__restrict__ grad, double dx2,
+                                                        Grid g, double *__restrict__ partial) {
+  double acc[2] = {0.0, 0.0};
+  const Bounded none{};
+  const FixC cA = fixc_of(0.5 * (1.0 - 0.5 * kTheta)), cB = fixc_of(0.125 * kTheta);
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < g.N;
+       n += (long)gridDim.x * blockDim.x) {
+    const int y = (int)(n / g.nx), x = (int)(n - (long)y * g.nx);
+    double p[8], gsel;
+    pull_adjoint<false>(pin, x, y, g, none, p, gsel);
+    const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
+    const double v[10] = {p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], rx, ry};
+    const int E = max_exp_n<10>(v);
+    double gx, gy;
+    if (E >= kEmin && E <= kEmax) {
+      long long P[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) P[k] = to_fix_alu(p[k], E);
+      const long long B1 = P[0] - P[2], B2 = P[1] - P[3], B3 = P[4] - P[6], B4 = P[5] - P[7];
+      const long long SX = mulfix(B1, cA) + mulfix(B3 - B4, cB);
+      const long long SY = mulfix(B2, cA) + mulfix(B3 + B4, cB);
+      gx = dx2 * from_fix((to_fix_alu(rx, E) >> 1) - SX, E);
+      gy = dx2 * from_fix((to_fix_alu(ry, E) >> 1) - SY, E);
+    } else {
+      double sx, sy;
+      force_sensitivity(p, sx, sy);
+      gx = dx2 * (0.5 * rx - sx);
+      gy = dx2 * (0.5 * ry - sy);
+    }
+    if (MODE == 0) {
+      grad[n] = gx;
+      grad[g.N + n] = gy;
+      acc[0] += gx;
+      acc[1] += gy;
+    } else {
+      acc[0] += __ldg(basis + n) * gx + __ldg(basis + g.N + n) * gy;
+      acc[1] += __ldg(basis + 2 * g.N + n) * gx + __ldg(basis + 3 * g.N + n) * gy;
+    }
+  }
+  __shared__ double sm[64];
+  block_sum<2>(acc, sm);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x * 2 + 0] = acc[0];
+    partial[blockIdx.x * 2 + 1] = acc[1];
+  }
+}
+
 // Young's-modulus gradient (Eq. optimality with E entering omega_beta(E) and, at
 // boundary nodes, gamma(E) and the Neumann rule):
 //   dJ/dE = - sum_n phi_S,n^T dC_n/dE - sum_n phi_C,n^T (dS'/dE f_C)_n,

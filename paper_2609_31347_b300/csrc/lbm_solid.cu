@@ -51,6 +51,7 @@ struct lbm_solid {
   uint8_t *negmask = nullptr;
   double *R = nullptr;
   long cblocks = 0;
+  long obj_parts = 0;  // partials of the last objective pass
   int ctpb = kCompactThreads;  // threads per block of every compact launch
   bool hoist = false;          // boundary loads issued up front (latency-bound grids)
   long nmon = 0;  // blocks that write monitor partials in a sweep
@@ -864,10 +865,21 @@ lbm_status check_opts(lbm_solid *h, const lbm_solve_opts *o) {
   return LBM_OK;
 }
 
+// Grid of the integer-pipe objective and gradient passes of periodic lattices.
+constexpr int kFixPassBlocks = 148 * 4;  // one wave at 64 registers, 256 threads
+
+// Objective partials and r; returns through obj_parts the number of partials written.
 lbm_status objective_partials(lbm_solid *h) {
   h->r_at = h->pstate;
   const double scale = h->dx * h->dx / h->cbar;
-  if (h->periodic) {
+  h->obj_parts = h->nblocks2d;
+  if (h->periodic && !h->fcur_is_fs && h->kernel != LBM_KERNEL_FP64) {
+    h->obj_parts = kFixPassBlocks;
+    if (h->obs)
+      k_objective_fix<true><<<kFixPassBlocks, 256, 0, h->stream>>>(h->fcur, h->g2, h->dstar, h->obs, h->r2, scale, h->grid, h->partial);
+    else
+      k_objective_fix<false><<<kFixPassBlocks, 256, 0, h->stream>>>(h->fcur, h->g2, h->dstar, nullptr, h->r2, scale, h->grid, h->partial);
+  } else if (h->periodic) {
     if (h->fcur_is_fs)
       k_objective<false, false><<<h->grd, h->blk, 0, h->stream>>>(h->fcur, h->g2, h->dstar, h->obs, h->r2, scale, h->grid, h->bnd, h->partial);
     else
@@ -1278,7 +1290,7 @@ lbm_status lbm_solid_objective(lbm_solid *h, double *J) {
   if (!h->have_target) return fail(h, LBM_ERR_STATE, "objective needs set_target first");
   lbm_status st = objective_partials(h);
   if (st) return st;
-  if ((st = finish(h, h->nblocks2d, 1, 0, 0.5 * h->dx * h->dx / h->cbar, h->dres))) return st;
+  if ((st = finish(h, h->obj_parts, 1, 0, 0.5 * h->dx * h->dx / h->cbar, h->dres))) return st;
   if ((st = fetch(h, 1))) return st;
   *J = h->hres[0];
   return LBM_OK;
@@ -1318,16 +1330,22 @@ lbm_status lbm_solid_gradient(lbm_solid *h, double *grad, size_t n, int project)
   if (!grad) return fail(h, LBM_ERR_ARG, "grad is NULL");
   if (!h->adjoint_valid) return fail(h, LBM_ERR_STATE, "gradient needs an adjoint solve at the current primal state");
   const double dx2 = h->dx * h->dx;
+  const bool fix = h->kernel != LBM_KERNEL_FP64;  // integer-pipe pass (periodic lattices)
   lbm_status st;
   if (h->control == LBM_CTRL_FORCE_FIELD) {
     if (n != (size_t)(2 * h->N)) return fail(h, LBM_ERR_ARG, "FORCE_FIELD gradient has 2N values");
-    if (h->periodic)
+    long parts = h->nblocks2d;
+    if (h->periodic && fix) {
+      parts = kFixPassBlocks;
+      k_grad_force_fix<0><<<kFixPassBlocks, 256, 0, h->stream>>>(h->pcur, h->r2, nullptr, grad, dx2, h->grid, h->partial);
+    } else if (h->periodic) {
       k_grad_force<false, 0><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, nullptr, grad, dx2, h->grid, h->bnd, h->partial);
-    else
+    } else {
       k_grad_force<true, 0><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, nullptr, grad, dx2, h->grid, h->bnd, h->partial);
+    }
     LAUNCHED(h);
     if (project) {
-      if ((st = finish(h, h->nblocks2d, 2, 0, 1.0 / (double)h->n_active, h->dres))) return st;
+      if ((st = finish(h, parts, 2, 0, 1.0 / (double)h->n_active, h->dres))) return st;
       if (h->periodic)
         k_subtract_mean<false><<<h->grd, h->blk, 0, h->stream>>>(grad, h->dres, h->grid, h->bnd);
       else
@@ -1338,12 +1356,17 @@ lbm_status lbm_solid_gradient(lbm_solid *h, double *grad, size_t n, int project)
   }
   if (h->control == LBM_CTRL_FORCE_BASIS2) {
     if (n != 2) return fail(h, LBM_ERR_ARG, "FORCE_BASIS2 gradient has 2 values");
-    if (h->periodic)
+    long parts = h->nblocks2d;
+    if (h->periodic && fix) {
+      parts = kFixPassBlocks;
+      k_grad_force_fix<1><<<kFixPassBlocks, 256, 0, h->stream>>>(h->pcur, h->r2, h->basis, nullptr, dx2, h->grid, h->partial);
+    } else if (h->periodic) {
       k_grad_force<false, 1><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, h->basis, nullptr, dx2, h->grid, h->bnd, h->partial);
-    else
+    } else {
       k_grad_force<true, 1><<<h->grd, h->blk, 0, h->stream>>>(h->pcur, h->r2, h->basis, nullptr, dx2, h->grid, h->bnd, h->partial);
+    }
     LAUNCHED(h);
-    return finish(h, h->nblocks2d, 2, 0, 1.0, grad);
+    return finish(h, parts, 2, 0, 1.0, grad);
   }
   if (h->control == LBM_CTRL_YOUNG_SCALAR) {
     if (n != 1) return fail(h, LBM_ERR_ARG, "YOUNG_SCALAR gradient has 1 value");
