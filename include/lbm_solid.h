@@ -25,19 +25,24 @@
  *   - Arithmetic of the sweeps (lbm_solid_desc.kernel):
  *       LBM_KERNEL_FP64: every operation in binary64 (relative rounding 2^-53 per
  *         operation).
- *       LBM_KERNEL_AUTO (default): the collision of each bulk node (periodic nodes and
- *         interior nodes of bounded grids; constant or per-node modulus) runs in 64-bit
- *         fixed point scaled to the node's largest input: the ten inputs of the node (8
+ *       LBM_KERNEL_AUTO (default): the collision of each node (periodic nodes, interior
+ *         nodes of bounded grids, and boundary nodes whose gamma-modified constants are
+ *         below 1/2 in magnitude; constant or per-node modulus) runs in 64-bit fixed
+ *         point scaled to the node's largest input: the ten inputs of the node (8
  *         populations, 2 force or adjoint-source values) are converted to integers at
  *         the scale 2^-56 of that largest input, combined exactly with integer adds and
  *         62-bit fixed-point constants, and rounded back to binary64.  Every output is
  *         within 4 * 2^-56 of the node's largest input of the exact value.  This is
  *         tighter than binary64 for values near the node's maximum, but a value much
  *         smaller than its node's maximum keeps fewer relative bits (a population 2^-40
- *         of the node's largest input keeps about 16).  Nodes whose largest input lies
- *         outside [2^-923, 2^57) (subnormal-only nodes, Inf and NaN), boundary
- *         nodes, reductions, objectives and gradients use binary64; a node whose
- *         inputs are all zero maps to zero exactly.
+ *         of the node's largest input keeps about 16).  On periodic lattices the
+ *         objective pass (e = d - d*) and the force gradient (r/2 - (dC/dg)^T phi_S)
+ *         form their per-node differences the same way (twelve and ten inputs, within
+ *         a few 2^-56 of the node's largest input) before binary64 products and sums.
+ *         Nodes whose largest input lies outside [2^-923, 2^57) (subnormal-only nodes,
+ *         Inf and NaN), the boundary rules, reductions, plate objectives and the
+ *         modulus gradients use binary64; a node whose inputs are all zero maps to
+ *         zero exactly.
  *   - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA tensors) on
  *     the handle's device; *_host are host pointers; desc arrays are host arrays.
  *     All caller pointers are borrowed for the duration of the call only.
