@@ -722,13 +722,17 @@ def eoc_ladders(torch, lbm, I, plate_sizes=(40, 80)):
             n_eval[0] += 1
             return fg0(a)
         s.sweeps.clear()
+        s.capped.clear()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = gbo.lbfgs(fg, a0, m_max=m_max, eps=eps, norm=norm, k_max=k_max)
         torch.cuda.synchronize()
         return r, {"s": time.perf_counter() - t0, "lbfgs_steps": r.steps, "stop": r.reason,
                    "evaluations": n_eval[0], "J": r.J, "grad_norm": r.grad_norm,
-                   "sweeps": int(sum(s.sweeps.values()))}
+                   "sweeps": int(sum(s.sweeps.values())),
+                   "sweeps_primal": int(s.sweeps.get("primal_solve", 0)),
+                   "sweeps_adjoint": int(s.sweeps.get("adjoint_solve", 0)),
+                   "adjoint_solves_at_t_max": int(s.capped.get("adjoint_solve", 0))}
 
     # distributed force control (Table 3: T_max = 10)
     rows = {}

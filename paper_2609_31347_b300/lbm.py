@@ -298,6 +298,7 @@ class LBMSolid:
         self.nx, self.ny, self.N = int(nx), int(ny), int(nx) * int(ny)
         self.dx, self.periodic = float(dx), bool(periodic)
         self.sweeps = {}  # sweeps performed per solve kind ("primal_solve", ...)
+        self.capped = {}  # solves per kind that ended at max_steps before their rule held
         self.control = control
         N = self.N
         keep = [_host(node_mask, np.uint8, N), _host(link_bc, np.uint8, 8 * N),
@@ -367,6 +368,8 @@ class LBMSolid:
         info = _Info()
         st = fn(self._h, ctypes.byref(o), ctypes.byref(info))
         self.sweeps[what] = self.sweeps.get(what, 0) + int(info.steps)
+        if st == LBM_ERR_NOT_CONVERGED:
+            self.capped[what] = self.capped.get(what, 0) + 1
         if st != LBM_OK and not (allow_not_converged and
                                  st in (LBM_ERR_NOT_CONVERGED, LBM_ERR_DIVERGED)):
             self._check(st, what)
