@@ -669,10 +669,11 @@ lbm_status loop_graph_for(lbm_solid *h, int kind, long c, cudaGraphExec_t &exec)
   if (e == cudaSuccess)
     e = cudaStreamBeginCaptureToGraph(h->cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess) {  // refused: the caller keeps the host loop (handle stays usable)
     cudaGraphDestroy(graph);
     cudaGetLastError();
-    return fail(h, LBM_ERR_CUDA, std::string("loop graph: ") + cudaGetErrorString(e));
+    h->err = std::string("loop graph: ") + cudaGetErrorString(e);
+    return LBM_ERR_STATE;
   }
   double *f0 = h->fcur, *f1 = h->fnext, *p0 = h->pcur, *p1 = h->pnext;
   cudaStream_t user = h->stream;
@@ -716,9 +717,10 @@ lbm_status loop_graph_for(lbm_solid *h, int kind, long c, cudaGraphExec_t &exec)
   cudaError_t ei = (el == cudaSuccess && ec == cudaSuccess) ? cudaGraphInstantiate(&ex, graph, 0)
                                                              : (el != cudaSuccess ? el : ec);
   cudaGraphDestroy(graph);
-  if (ei != cudaSuccess) {
+  if (ei != cudaSuccess) {  // as above
     cudaGetLastError();
-    return fail(h, LBM_ERR_CUDA, std::string("loop graph: ") + cudaGetErrorString(ei));
+    h->err = std::string("loop graph: ") + cudaGetErrorString(ei);
+    return LBM_ERR_STATE;
   }
   if (h->loops.size() >= 8) {
     cudaGraphExecDestroy(h->loops.front().exec);
@@ -756,11 +758,13 @@ lbm_status device_loop(lbm_solid *h, int kind, long c, long max_iters, double to
     ++h->launches;
   } else {
     cudaGraphExec_t ex = nullptr;
-    if (loop_graph_for(h, kind, c, ex) != LBM_OK) {
-      h->no_dloop = true;  // e.g. a launch form that capture into a conditional body refuses
+    const lbm_status ls = loop_graph_for(h, kind, c, ex);
+    if (ls == LBM_ERR_STATE) {  // capture into a conditional body refused: host loop
+      h->no_dloop = true;
       h->err.clear();
       return LBM_OK;
     }
+    if (ls) return ls;
     CK(h, cudaMemcpyAsync(h->dloop, h->hloop, sizeof(LoopState), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaGraphLaunch(ex, h->stream));
   }
