@@ -117,9 +117,10 @@ def test_objective_is_round_off_at_the_benchmark1_optimum():
         assert J1 > 1e-6
 
 
-# Independent values: a per-wavevector computation of the same steady errors written
-# separately from this oracle when the method was surveyed (readings R2-R7), printed to
-# five significant digits.  N_x = 32, 64, 128, 256; None where it printed no value.
+# Independent values: a per-wavevector computation of the same steady errors, written
+# separately from this oracle (same lattice units, force scaling g = dx^2 F and stress
+# scale), printed to five significant digits.  N_x = 32, 64, 128, 256; None where it
+# printed no value.
 INDEPENDENT = {
     "e_d_L2": [1.0395e-2, 2.6153e-3, 6.5486e-4, 1.6378e-4],
     "e_sigma_L2": [8.4374e-3, None, None, 1.3222e-4],
