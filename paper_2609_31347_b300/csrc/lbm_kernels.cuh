@@ -1377,17 +1377,18 @@ __device__ __forceinline__ void adjoint_item(const double *pin, double *pout,
 // (b after an odd count).  With monitor, the last sweep's partial sums of |d|^2 go to
 // partial[rank] and partial[ncta .. npartial) are zeroed, so the usual finishing pass
 // over npartial entries gives the monitor.  Launched as ONE cluster of gridDim.x CTAs.
-// With chunk > 0 (even) the kernel is the whole residual-rule solve loop instead: chunks
-// of `chunk` sweeps, each followed by the residual of its last two states and the
-// cluster-wide decision (cluster_residual_stop), at most max_iters chunks; ls receives
-// the chunks run and the last residual.
+// With chunk > 0 the kernel is the whole residual-rule solve loop instead: a first chunk
+// of `first` sweeps, then chunks of `chunk`, each followed by the residual of its last
+// two states and the cluster-wide decision (cluster_residual_stop), at most max_iters
+// chunks; ls receives the chunks run and the last residual (the state ends in b after
+// an odd total of sweeps, as for nsweeps).
 template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
 __global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
                                                     const double *__restrict__ src2, Grid g,
                                                     Bounded b, Compact c, Coef c0, Field fl,
                                                     ClusterWork w, int nsweeps, int monitor,
                                                     double *__restrict__ partial,
-                                                    long npartial, int chunk,
+                                                    long npartial, int chunk, int first,
                                                     long long max_iters, double tol,
                                                     LoopState *ls) {
   const unsigned rank = cluster_rank(), ncta = cluster_size();
@@ -1396,10 +1397,12 @@ __global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
   double mon[1] = {0.0};
   if (chunk > 0) {
     __shared__ double red[2], flag[2], smx[64];
+    int par = 0;  // sweeps run so far, mod 2: the latest state is in b2 when odd
     for (long long it = 0;; ++it) {
-      for (int s = 0; s < chunk; ++s) {
-        const double *in = (s & 1) ? b2 : a;
-        double *out = (s & 1) ? a : b2;
+      const int len = it == 0 ? first : chunk;
+      for (int s = 0; s < len; ++s) {
+        const double *in = par ? b2 : a;
+        double *out = par ? a : b2;
         for (long i = t0; i < w.nitems; i += T) {
           if (KIND == 0)
             primal_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, i, mon[0]);
@@ -1407,15 +1410,16 @@ __global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
             adjoint_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, i, mon[0]);
         }
         cluster_sync_release_acquire();
+        par ^= 1;
       }
-      // an even chunk leaves the latest state in a, the one before it in b2
+      const double *cur = par ? b2 : a, *prv = par ? a : b2;
       double v0 = 0.0, v1 = 0.0;
       for (long i = t0; i < w.nitems; i += T) {
         const long n = !BOUNDED ? i : (i < c.nb ? (long)c.bnode[i] : (long)w.inner[i - c.nb]);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const double ai = a[k * g.N + n];
-          v0 = nan_max(v0, fabs(ai - b2[k * g.N + n]));
+          const double ai = cur[k * g.N + n];
+          v0 = nan_max(v0, fabs(ai - prv[k * g.N + n]));
           v1 = nan_max(v1, fabs(ai));
         }
       }
@@ -1475,14 +1479,15 @@ __global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
 // Dynamic shared memory of k_sweeps_dsm: 18 doubles per node of the band.
 constexpr int kDsmDoublesPerNode = 18;
 
-// With chunk > 0 (even): the residual-rule solve loop as in k_sweeps_cl, the residual
-// read from the two shared-memory buffers.
+// With chunk > 0: the residual-rule solve loop as in k_sweeps_cl (a first chunk of
+// `first` sweeps, then chunks of `chunk`), the residual read from the two shared-memory
+// buffers.
 template <int KIND, int ARITH>
 __global__ void __launch_bounds__(512) k_sweeps_dsm(double *a, double *b2,
                                                      const double *__restrict__ src2, Grid g,
                                                      Coef c0, int h, int nsweeps, int monitor,
                                                      double *__restrict__ partial,
-                                                     long npartial, int chunk,
+                                                     long npartial, int chunk, int first,
                                                      long long max_iters, double tol,
                                                      LoopState *ls) {
   extern __shared__ __align__(16) double dsm[];
@@ -1502,16 +1507,18 @@ __global__ void __launch_bounds__(512) k_sweeps_dsm(double *a, double *b2,
   __shared__ double red[2], flag[2], smx[64];
   cluster_sync_release_acquire();
   long long it = 0;
-  const int per = chunk > 0 ? chunk : nsweeps;
+  long total = 0;  // sweeps run; the latest state is in B1 when odd
+  int len = chunk > 0 ? first : nsweeps;
   for (int s = 0;; ++s) {
-    if (s == per) {  // end of a chunk (loop mode) or of the run
+    if (s == len) {  // end of a chunk (loop mode) or of the run
       if (chunk <= 0) break;
-      double v0 = 0.0, v1 = 0.0;  // an even chunk: latest state in B0, the one before in B1
+      const double *cur = (total & 1) ? B1 : B0, *prv = (total & 1) ? B0 : B1;
+      double v0 = 0.0, v1 = 0.0;
       for (long l = threadIdx.x; l < L; l += blockDim.x) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const double ai = B0[k * L + l];
-          v0 = nan_max(v0, fabs(ai - B1[k * L + l]));
+          const double ai = cur[k * L + l];
+          v0 = nan_max(v0, fabs(ai - prv[k * L + l]));
           v1 = nan_max(v1, fabs(ai));
         }
       }
@@ -1524,9 +1531,10 @@ __global__ void __launch_bounds__(512) k_sweeps_dsm(double *a, double *b2,
       }
       ++it;
       s = 0;
+      len = chunk;
     }
-    const double *S = (s & 1) ? B1 : B0;
-    double *D = (s & 1) ? B0 : B1;
+    const double *S = (total & 1) ? B1 : B0;
+    double *D = (total & 1) ? B0 : B1;
     const unsigned Sa = smem_addr(S);
     const bool last_mon = chunk <= 0 && monitor && s == nsweeps - 1;
     for (long l = threadIdx.x; l < L; l += blockDim.x) {
@@ -1569,9 +1577,10 @@ __global__ void __launch_bounds__(512) k_sweeps_dsm(double *a, double *b2,
       if (last_mon) mon[0] += m1 * m1 + m2 * m2;
     }
     cluster_sync_release_acquire();
+    ++total;
   }
-  if (per > 0) {
-    const bool odd = chunk <= 0 && (nsweeps & 1);
+  if (total > 0) {
+    const bool odd = total & 1;
     const double *fin = odd ? B1 : B0, *prev = odd ? B0 : B1;
     double *gfin = odd ? b2 : a, *gprev = odd ? a : b2;
     for (long l = threadIdx.x; l < L; l += blockDim.x) {

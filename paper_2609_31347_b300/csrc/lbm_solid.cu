@@ -285,7 +285,7 @@ constexpr long kClusterChunk = 512;           // sweeps per launch (fixed-step r
 template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
 cudaError_t launch_cluster(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
                            int *fits = nullptr, int chunk = 0, long long max_iters = 0,
-                           double tol = 0.0) {
+                           double tol = 0.0, int first = 0) {
   auto kern = k_sweeps_cl<KIND, BOUNDED, ARITH, FIELD>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h->cl_ncta);
@@ -307,20 +307,20 @@ cudaError_t launch_cluster(lbm_solid *h, int nsweeps, bool monitor, bool probe =
   const double *src = KIND == 0 ? h->g2 : h->r2;
   return cudaLaunchKernelEx(&cfg, kern, a, b, src, h->grid, h->bnd, h->cmp, h->coef, h->fl,
                             h->cw, nsweeps, monitor ? 1 : 0, h->partial, h->nmon, chunk,
-                            max_iters, tol, h->dloop);
+                            first, max_iters, tol, h->dloop);
 }
 
 // (periodic lattices only: bounded grids measured no gain, see kClusterMaxItems)
 template <int KIND>
 cudaError_t launch_cluster_any(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
                                int *fits = nullptr, int chunk = 0, long long max_iters = 0,
-                               double tol = 0.0) {
+                               double tol = 0.0, int first = 0) {
   const bool fp = h->kernel == LBM_KERNEL_FP64;
   if (h->field)
-    return fp ? launch_cluster<KIND, false, 0, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol)
-              : launch_cluster<KIND, false, 1, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol);
-  return fp ? launch_cluster<KIND, false, 0, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol)
-            : launch_cluster<KIND, false, 1, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol);
+    return fp ? launch_cluster<KIND, false, 0, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first)
+              : launch_cluster<KIND, false, 1, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first);
+  return fp ? launch_cluster<KIND, false, 0, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first)
+            : launch_cluster<KIND, false, 1, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first);
 }
 
 // Launch shape of the compact sweep of a bounded grid.  Below ~32 warps per SM the sweep
@@ -352,7 +352,7 @@ constexpr long kDsmBandNodes = 128;
 template <int KIND, int ARITH>
 cudaError_t launch_dsm(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
                        int *fits = nullptr, int chunk = 0, long long max_iters = 0,
-                       double tol = 0.0) {
+                       double tol = 0.0, int first = 0) {
   auto kern = k_sweeps_dsm<KIND, ARITH>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h->dsm_ncta);
@@ -376,17 +376,17 @@ cudaError_t launch_dsm(lbm_solid *h, int nsweeps, bool monitor, bool probe = fal
   double *a = KIND == 0 ? h->fcur : h->pcur, *b = KIND == 0 ? h->fnext : h->pnext;
   const double *src = KIND == 0 ? h->g2 : h->r2;
   return cudaLaunchKernelEx(&cfg, kern, a, b, src, h->grid, h->coef, h->dsm_h, nsweeps,
-                            monitor ? 1 : 0, h->partial, h->nmon, chunk, max_iters, tol,
-                            h->dloop);
+                            monitor ? 1 : 0, h->partial, h->nmon, chunk, first, max_iters,
+                            tol, h->dloop);
 }
 
 template <int KIND>
 cudaError_t launch_dsm_any(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
                            int *fits = nullptr, int chunk = 0, long long max_iters = 0,
-                           double tol = 0.0) {
+                           double tol = 0.0, int first = 0) {
   return h->kernel == LBM_KERNEL_FP64
-             ? launch_dsm<KIND, 0>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol)
-             : launch_dsm<KIND, 1>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol);
+             ? launch_dsm<KIND, 0>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first)
+             : launch_dsm<KIND, 1>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first);
 }
 
 // Chooses the cluster for a lattice held in distributed shared memory: C CTAs with C
@@ -731,10 +731,11 @@ lbm_status loop_graph_for(lbm_solid *h, int kind, long c, cudaGraphExec_t &exec)
   return LBM_OK;
 }
 
-// Runs up to max_iters chunks of c sweeps on the device (residual rule); returns the
+// Runs up to max_iters chunks on the device (residual rule): a first chunk of `first`
+// sweeps (cluster-resident lattices only; c otherwise), then chunks of c; returns the
 // chunks run and the last residual.  ok = false when no loop graph can be built (the
 // caller keeps the host loop).
-lbm_status device_loop(lbm_solid *h, int kind, long c, long max_iters, double tol,
+lbm_status device_loop(lbm_solid *h, int kind, long c, long first, long max_iters, double tol,
                        long &iters, double &metric, bool &ok) {
   ok = false;
   if (h->no_dloop) return LBM_OK;
@@ -743,20 +744,23 @@ lbm_status device_loop(lbm_solid *h, int kind, long c, long max_iters, double to
     CK(h, cudaMallocHost((void **)&h->hloop, sizeof(LoopState)));
   }
   *h->hloop = LoopState{tol, max_iters, 0, 0.0};
-  if (h->dsm_ncta > 0 || h->cl_ncta > 0) {
+  const bool cluster = h->dsm_ncta > 0 || h->cl_ncta > 0;
+  if (cluster) {
     // a cluster-resident lattice: the kernel itself loops over the chunks
-    if (c > INT32_MAX) return LBM_OK;
+    if (c > INT32_MAX || first < 1 || first > c) return LBM_OK;
     CK(h, cudaMemcpyAsync(h->dloop, h->hloop, sizeof(LoopState), cudaMemcpyHostToDevice, h->stream));
+    const int ci = (int)c, fi = (int)first;
     const cudaError_t e =
         h->dsm_ncta > 0
-            ? (kind == 0 ? launch_dsm_any<0>(h, 0, false, false, nullptr, (int)c, max_iters, tol)
-                         : launch_dsm_any<1>(h, 0, false, false, nullptr, (int)c, max_iters, tol))
-            : (kind == 0 ? launch_cluster_any<0>(h, 0, false, false, nullptr, (int)c, max_iters, tol)
-                         : launch_cluster_any<1>(h, 0, false, false, nullptr, (int)c, max_iters, tol));
+            ? (kind == 0 ? launch_dsm_any<0>(h, 0, false, false, nullptr, ci, max_iters, tol, fi)
+                         : launch_dsm_any<1>(h, 0, false, false, nullptr, ci, max_iters, tol, fi))
+            : (kind == 0 ? launch_cluster_any<0>(h, 0, false, false, nullptr, ci, max_iters, tol, fi)
+                         : launch_cluster_any<1>(h, 0, false, false, nullptr, ci, max_iters, tol, fi));
     if (e != cudaSuccess)
       return fail(h, LBM_ERR_CUDA, std::string("cluster loop launch: ") + cudaGetErrorString(e));
     ++h->launches;
   } else {
+    if (first != c) return LBM_OK;
     cudaGraphExec_t ex = nullptr;
     const lbm_status ls = loop_graph_for(h, kind, c, ex);
     if (ls == LBM_ERR_STATE) {  // capture into a conditional body refused: host loop
@@ -772,7 +776,11 @@ lbm_status device_loop(lbm_solid *h, int kind, long c, long max_iters, double to
   CK(h, cudaStreamSynchronize(h->stream));
   iters = (long)h->hloop->iters;
   metric = h->hloop->metric;
-  if (!(h->dsm_ncta > 0 || h->cl_ncta > 0)) h->launches += iters * (c + 3);
+  if (!cluster) h->launches += iters * (c + 3);
+  if (cluster && iters > 0 && ((first + (iters - 1) * c) & 1)) {  // state ended in b
+    if (kind == 0) std::swap(h->fcur, h->fnext);
+    else std::swap(h->pcur, h->pnext);
+  }
   if (kind == 0) ++h->pstate;
   ok = true;
   return LBM_OK;
@@ -794,7 +802,31 @@ lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *inf
     std::deque<double> win;
     h->samples.clear();
     bool done = false;
-    while (!done && steps < o->max_steps) {
+    // residual rule on a cluster-resident lattice: one launch runs every whole chunk (the
+    // collide-only or from-rest first sweep, when due, is launched just before and
+    // counts towards the first chunk)
+    const long ce = o->check_every;
+    if (o->criterion == 1 && (h->dsm_ncta > 0 || h->cl_ncta > 0) && ce % 2 == 0 &&
+        ce <= INT32_MAX && o->max_steps >= ce) {
+      long pre = 0;
+      if ((kind == 0 && h->fcur_is_fs) || (kind == 1 && h->pcur_rest)) {
+        lbm_status st = run_sweeps(h, kind, 1, false);
+        if (st) return st;
+        pre = 1;
+      }
+      long iters = 0;
+      double mv = 0.0;
+      bool ok = false;
+      lbm_status st = device_loop(h, kind, ce, ce - pre, o->max_steps / ce, o->tol, iters, mv, ok);
+      if (st) return st;
+      steps = ok ? iters * ce : pre;
+      if (ok) {
+        metric = mv;
+        if (std::isnan(mv)) result = LBM_ERR_DIVERGED;
+        else if (mv < o->tol) done = true;
+      }
+    }
+    while (result == LBM_OK && !done && steps < o->max_steps) {
       long k = o->check_every;
       if (k > o->max_steps - steps) k = o->max_steps - steps;
       // a chunk whose only sweep is the collide-only first sweep has no monitor value
@@ -835,7 +867,7 @@ lbm_status solve_loop(lbm_solid *h, const lbm_solve_opts *o, lbm_solve_info *inf
           long iters = 0;
           double mv = 0.0;
           bool ok = false;
-          if ((st = device_loop(h, kind, c, iters_max, o->tol, iters, mv, ok))) return st;
+          if ((st = device_loop(h, kind, c, c, iters_max, o->tol, iters, mv, ok))) return st;
           if (ok) {
             steps += iters * c;
             metric = mv;
