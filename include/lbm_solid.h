@@ -151,7 +151,7 @@ lbm_status lbm_solid_set_control(lbm_solid *h, const double *alpha_dev, size_t n
 /* Target displacement d* on the device (2N); computes Cbar of Eq. node_J. */
 lbm_status lbm_solid_set_target(lbm_solid *h, const double *dstar_dev);
 
-/* Primal solve (Algorithm 2, line 3): sweeps from the current f_S until opts'
+/* Primal solve (Algorithm 2, the primal step): sweeps from the current f_S until opts'
    rule holds.  Returns LBM_ERR_NOT_CONVERGED / LBM_ERR_DIVERGED accordingly (the
    state is kept either way).  info may be NULL. */
 lbm_status lbm_solid_primal_solve(lbm_solid *h, const lbm_solve_opts *opts,

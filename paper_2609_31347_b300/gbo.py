@@ -1,7 +1,7 @@
 """Gradient-based optimisation on top of the CUDA solver (host orchestration).
 
 - ``LBMObjective``: a ``torch.autograd.Function`` whose forward runs the primal solve
-  and the objective (Algorithm 2, line 3) and whose backward runs the adjoint solve and
+  and the objective (Algorithm 2, its primal step) and whose backward runs the adjoint solve and
   the gradient (Algorithm 1, Eq. optimality).  A control at which the primal iteration
   diverges (no steady state, e.g. a modulus that makes the boundary collision singular)
   gets J = +inf, so that the line search steps back.  Only the steady primal state f_S is kept
