@@ -125,7 +125,10 @@ typedef struct {
                           (Eq. convergence_crit);
                        1: residual max|f_C(t)-f_C(t-1)| / max|f_C(t)| < tol             */
   long window;      /* criterion 0: number of samples in the window (>= 2)              */
-  long check_every; /* sweeps between monitor samples (>= 1)                            */
+  long check_every; /* sweeps between monitor samples (>= 1).  With criterion 1 and an
+                       even check_every the chunks and their tests run on the device
+                       (no host round trip per test); the stopping sweep and the state
+                       are the same as those of the rule evaluated on the host            */
   int fixed_steps;  /* nonzero: run exactly max_steps sweeps, no stopping test           */
 } lbm_solve_opts;
 
