@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kThreads) k_primal_batch(const double *__restr
   double f[8], gsel, o[8], dxn, dyn;
   pull_primal<false>(fin, x, y, g, b, f, gsel);
   const double qx = __ldg(q + n), qy = __ldg(q + g.N + n);
-  if (ARITH == 0 || !collide_fix<false>(f, qx, qy, c.fx, o, dxn, dyn))
+  if (ARITH == 0 || !collide_fix<false, false, true, true>(f, qx, qy, c.fx, o, dxn, dyn))
     collide<false>(f, qx, qy, c, o, dxn, dyn);
 #pragma unroll
   for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_collide_batch(const double *__rest
   double f[8], o[8], dxn, dyn;
 #pragma unroll
   for (int k = 0; k < 8; ++k) f[k] = fin[k * I.N + n];
-  if (ARITH == 0 || !collide_fix<false>(f, q[n], q[I.N + n], c.fx, o, dxn, dyn))
+  if (ARITH == 0 || !collide_fix<false, false, true, true>(f, q[n], q[I.N + n], c.fx, o, dxn, dyn))
     collide<false>(f, q[n], q[I.N + n], c, o, dxn, dyn);
 #pragma unroll
   for (int k = 0; k < 8; ++k) fout[k * I.N + n] = o[k];
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_batch(const double *__rest
   double p[8], gsel, o[8], ax, ay;
   pull_adjoint<false>(pin, x, y, g, b, p, gsel);
   const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
-  if (ARITH == 0 || !collide_T_fix<false, false, true>(p, rx, ry, c.fx, o, ax, ay))
+  if (ARITH == 0 || !collide_T_fix<false, false, true, true, true>(p, rx, ry, c.fx, o, ax, ay))
     collide_T<false>(p, rx, ry, c, o, ax, ay);
 #pragma unroll
   for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];

@@ -87,6 +87,25 @@ __device__ __forceinline__ double from_fix(long long v, int E) {
   return __longlong_as_double(a == 0 ? 0ll : (long long)bits);
 }
 
+// The same value through the hardware conversion: v converted to binary64 (round to
+// nearest even; exact below 2^53) and scaled by 2^(E-1079) in the exponent field, which
+// stays in the normal range for |v| >= 1 and E in [kEmin, kEmax].  Three instructions
+// against ~20, at the price of one conversion on the FP64 pipe per value: the periodic
+// sweeps, which also convert their inputs on the integer pipes (ALU_POP), take it
+// (measured at 4096^2: primal 0.410 -> 0.395 ms, adjoint 0.396 -> 0.392 ms per sweep);
+// the plate kernels, on which it measured slower, keep from_fix.  Ties round to even
+// instead of away from zero; the bound of a half unit in the last place is the same.
+__device__ __forceinline__ double from_fix_cvt(long long v, int E) {
+  const double d = __ll2double_rn(v);
+  const int hi = __double2hiint(d) + ((E - 1079) << 20);
+  return v == 0 ? 0.0 : __hiloint2double(hi, __double2loint(d));
+}
+
+template <bool CVT>
+__device__ __forceinline__ double fix_out(long long v, int E) {
+  return CVT ? from_fix_cvt(v, E) : from_fix(v, E);
+}
+
 // A node whose ten inputs are all +0 or -0 maps to zero (the collision and its transpose
 // are linear): writes zeros and returns true, else returns false.  Tried only on nodes
 // that the fixed-point path declined, before the FP64-pipe path.
@@ -115,8 +134,9 @@ __device__ __forceinline__ int max_exp10(const double (&f)[8], double a, double 
 // Collision in fixed point (same map as collide<BND>; boundary rows use qs_b, P_b).
 // Returns false when the node must take the FP64-pipe path (largest exponent outside
 // [kEmin, kEmax]).  ALU_POP converts the eight populations on the integer pipes as well
-// (the same values: both conversions truncate the same product).
-template <bool MON, bool BND = false, bool ALU_POP = BND>
+// (the same values: both conversions truncate the same product); CVT rounds the outputs
+// back with from_fix_cvt.
+template <bool MON, bool BND = false, bool ALU_POP = BND, bool CVT = false>
 __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, double qy,
                                             const CoefFix &c, double (&o)[8], double &dx_,
                                             double &dy_) {
@@ -143,25 +163,25 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
   const long long o1 = t10 + QX, o2 = t01 + QY;
   const long long u = (t10 + t01) >> 2, v = (t01 - t10) >> 2;
   const long long q11 = mulfix(m11, c.q11);
-  o[0] = from_fix(e1 + o1, E);
-  o[2] = from_fix(e1 - o1, E);
-  o[1] = from_fix(e2 + o2, E);
-  o[3] = from_fix(e2 - o2, E);
+  o[0] = fix_out<CVT>(e1 + o1, E);
+  o[2] = fix_out<CVT>(e1 - o1, E);
+  o[1] = fix_out<CVT>(e2 + o2, E);
+  o[3] = fix_out<CVT>(e2 - o2, E);
   if (BND) {
     const long long P = mulfix(ms, c.P_b);  // m22^C / 4 = -gamma m_s^C / 4
-    o[4] = from_fix((P + q11) + u, E);
-    o[6] = from_fix((P + q11) - u, E);
-    o[5] = from_fix((P - q11) + v, E);
-    o[7] = from_fix((P - q11) - v, E);
+    o[4] = fix_out<CVT>((P + q11) + u, E);
+    o[6] = fix_out<CVT>((P + q11) - u, E);
+    o[5] = fix_out<CVT>((P - q11) + v, E);
+    o[7] = fix_out<CVT>((P - q11) - v, E);
   } else {
-    o[4] = from_fix(q11 + u, E);
-    o[6] = from_fix(q11 - u, E);
-    o[5] = from_fix(v - q11, E);
-    o[7] = from_fix(-q11 - v, E);
+    o[4] = fix_out<CVT>(q11 + u, E);
+    o[6] = fix_out<CVT>(q11 - u, E);
+    o[5] = fix_out<CVT>(v - q11, E);
+    o[7] = fix_out<CVT>(-q11 - v, E);
   }
   if (MON) {
-    dx_ = from_fix(mb10, E);
-    dy_ = from_fix(mb01, E);
+    dx_ = fix_out<CVT>(mb10, E);
+    dy_ = fix_out<CVT>(mb01, E);
   }
   return true;
 }
@@ -170,7 +190,7 @@ __device__ __forceinline__ bool collide_fix(const double (&f)[8], double qx, dou
 // two source values on the integer pipes (to_fix_alu) instead of the FP64 pipe: measured
 // faster for the batched adjoint (2.59 -> 2.50 ms per sweep of 97 M nodes), slower for one
 // 4096^2 lattice (0.388 -> 0.392 ms), so each kernel picks.
-template <bool MON, bool BND = false, bool ALU_SRC = false, bool ALU_POP = BND>
+template <bool MON, bool BND = false, bool ALU_SRC = false, bool ALU_POP = BND, bool CVT = false>
 __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, double ry,
                                               const CoefFix &c, double (&o)[8], double &ax,
                                               double &ay) {
@@ -196,19 +216,19 @@ __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, d
                            : mulfix(A1 + A2, c.qs);
   const long long nd = mulfix(A1 - A2, c.qd);
   const long long S1 = ns + nd, S2 = ns - nd;
-  o[0] = from_fix(S1 + n10, E);
-  o[2] = from_fix(S1 - n10, E);
-  o[1] = from_fix(S2 + n01, E);
-  o[3] = from_fix(S2 - n01, E);
+  o[0] = fix_out<CVT>(S1 + n10, E);
+  o[2] = fix_out<CVT>(S1 - n10, E);
+  o[1] = fix_out<CVT>(S2 + n01, E);
+  o[3] = fix_out<CVT>(S2 - n01, E);
   const long long T1 = 2 * ns + n11, T2 = 2 * ns - n11;
   const long long P1 = n10 + n01, P2 = n01 - n10;
-  o[4] = from_fix(T1 + P1, E);
-  o[6] = from_fix(T1 - P1, E);
-  o[5] = from_fix(T2 + P2, E);
-  o[7] = from_fix(T2 - P2, E);
+  o[4] = fix_out<CVT>(T1 + P1, E);
+  o[6] = fix_out<CVT>(T1 - P1, E);
+  o[5] = fix_out<CVT>(T2 + P2, E);
+  o[7] = fix_out<CVT>(T2 - P2, E);
   if (MON) {
-    ax = from_fix(B1 + d34, E);
-    ay = from_fix(B2 + s34, E);
+    ax = fix_out<CVT>(B1 + d34, E);
+    ay = fix_out<CVT>(B2 + s34, E);
   }
   return true;
 }

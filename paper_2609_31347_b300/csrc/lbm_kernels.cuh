@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_primal(const double *__restrict__ fin,
       if (BOUNDED && gsel != 0.0)
         collide<true>(f, qx, qy, c, o, dxn, dyn);
       else if (ARITH == 0 ||
-               !collide_fix<MONITOR>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
+               !collide_fix<MONITOR, false, !BOUNDED, !BOUNDED>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
         collide<false>(f, qx, qy, c, o, dxn, dyn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) fout[k * g.N + n] = o[k];
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_collide_only(const double *__restrict__
   const double qx = g2[n], qy = g2[g.N + n];
   if (bnd)
     collide<true>(f, qx, qy, c, o, dxn, dyn);
-  else if (ARITH == 0 || !collide_fix<false>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o,
+  else if (ARITH == 0 || !collide_fix<false, false, !BOUNDED, !BOUNDED>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o,
                                              dxn, dyn))
     collide<false>(f, qx, qy, c, o, dxn, dyn);
 #pragma unroll
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const double *__restrict__ pin,
       if (BOUNDED && gsel != 0.0)
         collide_T<true>(p, rx, ry, c, o, ax, ay);
       else if (ARITH == 0 ||
-               !collide_T_fix<MONITOR>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
+               !collide_T_fix<MONITOR, false, false, !BOUNDED, !BOUNDED>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
         collide_T<false>(p, rx, ry, c, o, ax, ay);
 #pragma unroll
       for (int k = 0; k < 8; ++k) pout[k * g.N + n] = o[k];
@@ -1329,7 +1329,7 @@ __device__ __forceinline__ void primal_item(const double *fin, double *fout,
     }
     const double qx = __ldg(g2 + n), qy = __ldg(g2 + g.N + n);
     if (ARITH == 0 ||
-        !collide_fix<MON>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
+        !collide_fix<MON, false, !BOUNDED, !BOUNDED>(f, qx, qy, node_fix<FIELD>(c0.fx, fl, g.N, n), o, dxn, dyn))
       if (ARITH == 0 || !zero_node(f, qx, qy, o))
         collide<false>(f, qx, qy, node_coef<FIELD>(c0, fl, g.N, n, -1), o, dxn, dyn);
   }
@@ -1367,7 +1367,7 @@ __device__ __forceinline__ void adjoint_item(const double *pin, double *pout,
     }
     const double rx = __ldg(r + n), ry = __ldg(r + g.N + n);
     if (ARITH == 0 ||
-        !collide_T_fix<MON>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
+        !collide_T_fix<MON, false, false, !BOUNDED, !BOUNDED>(p, rx, ry, node_fix<FIELD>(c0.fx, fl, g.N, n), o, ax, ay))
       if (ARITH == 0 || !zero_node(p, rx, ry, o))
         collide_T<false>(p, rx, ry, node_coef<FIELD>(c0, fl, g.N, n, -1), o, ax, ay);
   }
@@ -1561,17 +1561,17 @@ __global__ void __launch_bounds__(512) k_sweeps_dsm(double *a, double *b2,
       const double qx = Q[l], qy = Q[L + l];
       if (KIND == 0) {
         if (last_mon) {
-          if (ARITH == 0 || !collide_fix<true, false, true>(f, qx, qy, c0.fx, o, m1, m2))
+          if (ARITH == 0 || !collide_fix<true, false, true, true>(f, qx, qy, c0.fx, o, m1, m2))
             collide<false>(f, qx, qy, c0, o, m1, m2);
-        } else if (ARITH == 0 || !collide_fix<false, false, true>(f, qx, qy, c0.fx, o, m1, m2)) {
+        } else if (ARITH == 0 || !collide_fix<false, false, true, true>(f, qx, qy, c0.fx, o, m1, m2)) {
           collide<false>(f, qx, qy, c0, o, m1, m2);
         }
       } else {
         if (last_mon) {
-          if (ARITH == 0 || !collide_T_fix<true, false, false, true>(f, qx, qy, c0.fx, o, m1, m2))
+          if (ARITH == 0 || !collide_T_fix<true, false, false, true, true>(f, qx, qy, c0.fx, o, m1, m2))
             collide_T<false>(f, qx, qy, c0, o, m1, m2);
         } else if (ARITH == 0 ||
-                   !collide_T_fix<false, false, false, true>(f, qx, qy, c0.fx, o, m1, m2)) {
+                   !collide_T_fix<false, false, false, true, true>(f, qx, qy, c0.fx, o, m1, m2)) {
           collide_T<false>(f, qx, qy, c0, o, m1, m2);
         }
       }
