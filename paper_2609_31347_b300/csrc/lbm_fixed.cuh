@@ -57,13 +57,13 @@ __device__ __forceinline__ long long to_fix(double x, int sh20) {
 // The same value with integer operations only: x = M 2^(e - 1075) with M the 53-bit
 // significand and e the biased exponent, so the result is M shifted left by
 // e - E + 4 <= 4 places (right when negative, which truncates); zero and subnormal x
-// (e = 0) give 0.  The primal collision converts its two force values this way and its
-// eight populations with to_fix, which moves work from the FP64 pipe (which runs the
-// conversion instruction) to the integer pipes (measured: primal sweep 0.411 -> 0.406
-// ms at 4096^2; the transposed collision, slower that way, keeps to_fix for bulk nodes).
-// Boundary nodes (BND) convert all ten inputs this way: their rules already load the
-// FP64 pipe, and a boundary warp is the critical path of a small plate's sweep
-// (measured 2-4 % per sweep at N_x = 64 .. 512).
+// (e = 0) give 0.  Which conversion a kernel uses is a balance of its FP64 and integer
+// pipes: the plate kernels convert populations with to_fix and the force values this
+// way (primal sweep 0.411 -> 0.406 ms when measured on the 4096^2 lattice); boundary
+// nodes (BND) convert all ten inputs this way, since their rules already load the FP64
+// pipe and a boundary warp is the critical path of a small plate's sweep (2-4 % per
+// sweep at N_x = 64 .. 512); the periodic sweeps convert all inputs this way and give
+// the FP64 pipe the output conversions instead (from_fix_cvt).
 __device__ __forceinline__ long long to_fix_alu(double x, int E) {
   const long long b = __double_as_longlong(x);
   const int e = (int)(b >> 52) & 0x7ff;
