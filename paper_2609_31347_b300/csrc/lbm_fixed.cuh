@@ -233,4 +233,94 @@ __device__ __forceinline__ bool collide_T_fix(const double (&p)[8], double rx, d
   return true;
 }
 
+// ---------------------------------------------------------------------------------
+// Pair form of the bulk collisions: two adjacent lanes (h = lane & 1) share one node, so
+// that a lattice too small to give every SM sub-partition a warp of its own still uses
+// them, each lane running ~60 % of the single-lane instruction chain.  Lane h holds the
+// populations k = h, h + 2, h + 4, h + 6 (in[0..3]) and the force (adjoint source)
+// component h; it returns the outputs k = h, h + 2, h + 4, h + 6.  The integer operations
+// are those of collide_fix / collide_T_fix with ALU_POP (exact integer sums in another
+// grouping), so the results are bit-identical.  Every lane of the warp must take part
+// (warp shuffles); both lanes of a pair return the same flag.
+
+__device__ __forceinline__ long long xor1(long long v) {
+  return __shfl_xor_sync(0xffffffffu, v, 1);
+}
+
+// largest biased exponent of the pair's ten inputs
+__device__ __forceinline__ int pair_max_exp(const double (&in)[4], double q) {
+  int m = __double2hiint(q) & 0x7fffffff;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) m = max(m, __double2hiint(in[i]) & 0x7fffffff);
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  return m >> 20;
+}
+
+template <bool MON, bool CVT>
+__device__ __forceinline__ bool collide_fix_pair(const double (&in)[4], double q, int h,
+                                                 const CoefFix &c, double (&out)[4],
+                                                 double &m) {
+  const int E = pair_max_exp(in, q);
+  if (E < kEmin || E > kEmax) return false;
+  long long F[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) F[i] = to_fix_alu(in[i], E);
+  const long long Q = to_fix_alu(q, E);
+  const long long a = F[0] + F[1], b = F[0] - F[1];    // h = 0: a1, b1;  h = 1: a2, b2
+  const long long ad = F[2] + F[3], bd = F[2] - F[3];  // h = 0: a3, b3;  h = 1: a4, b4
+  const long long a_o = xor1(a), ad_o = xor1(ad), bd_o = xor1(bd);
+  const long long a1 = h ? a_o : a, a2 = h ? a : a_o;
+  const long long a3 = h ? ad_o : ad, a4 = h ? ad : ad_o;
+  const long long b3 = h ? bd_o : bd, b4 = h ? bd : bd_o;
+  const long long mb = b + (h ? (b3 + b4) : (b3 - b4)) + 2 * Q;  // mb10 / mb01
+  const long long ms = a1 + a2 + 2 * (a3 + a4);
+  const long long es = mulfix(ms, c.qs), td = mulfix(a1 - a2, c.qd);
+  const long long e = h ? es - td : es + td;                     // e1 / e2
+  const long long t = mulfix(mb, c.third);                       // t10 / t01
+  const long long t_o = xor1(t);
+  const long long t10 = h ? t_o : t, t01 = h ? t : t_o;
+  const long long oa = t + Q;                                    // o1 / o2
+  const long long u = (t10 + t01) >> 2, v = (t01 - t10) >> 2;
+  const long long q11 = mulfix(a3 - a4, c.q11);
+  out[0] = fix_out<CVT>(e + oa, E);
+  out[1] = fix_out<CVT>(e - oa, E);
+  out[2] = fix_out<CVT>(h ? v - q11 : q11 + u, E);
+  out[3] = fix_out<CVT>(h ? -q11 - v : q11 - u, E);
+  if (MON) m = fix_out<CVT>(mb, E);                              // d_x / d_y
+  return true;
+}
+
+template <bool MON, bool CVT>
+__device__ __forceinline__ bool collide_T_fix_pair(const double (&in)[4], double r, int h,
+                                                   const CoefFix &c, double (&out)[4],
+                                                   double &m) {
+  const int E = pair_max_exp(in, r);
+  if (E < kEmin || E > kEmax) return false;
+  long long P[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) P[i] = to_fix_alu(in[i], E);
+  const long long R = to_fix_alu(r, E);
+  const long long A = P[0] + P[1], B = P[0] - P[1];    // A1, B1 / A2, B2
+  const long long Ad = P[2] + P[3], Bd = P[2] - P[3];  // A3, B3 / A4, B4
+  const long long A_o = xor1(A), Ad_o = xor1(Ad), Bd_o = xor1(Bd);
+  const long long A1 = h ? A_o : A, A2 = h ? A : A_o;
+  const long long A3 = h ? Ad_o : Ad, A4 = h ? Ad : Ad_o;
+  const long long B3 = h ? Bd_o : Bd, B4 = h ? Bd : Bd_o;
+  const long long dd = h ? B3 + B4 : B3 - B4;                    // d34 / s34
+  const long long n = mulfix(B + (dd >> 2), c.third) - R;        // n10 / n01
+  const long long n_o = xor1(n);
+  const long long n10 = h ? n_o : n, n01 = h ? n : n_o;
+  const long long n11 = mulfix(A3 - A4, c.q11);
+  const long long ns = mulfix(A1 + A2, c.qs), nd = mulfix(A1 - A2, c.qd);
+  const long long S = h ? ns - nd : ns + nd;                     // S1 / S2
+  const long long T = h ? 2 * ns - n11 : 2 * ns + n11;           // T1 / T2
+  const long long Pp = h ? n01 - n10 : n10 + n01;                // P1 / P2
+  out[0] = fix_out<CVT>(S + n, E);
+  out[1] = fix_out<CVT>(S - n, E);
+  out[2] = fix_out<CVT>(T + Pp, E);
+  out[3] = fix_out<CVT>(T - Pp, E);
+  if (MON) m = fix_out<CVT>(B + dd, E);                          // a_x / a_y
+  return true;
+}
+
 }  // namespace lbm

@@ -1376,6 +1376,87 @@ __device__ __forceinline__ void adjoint_item(const double *pin, double *pout,
   if (MON) mon += ax * ax + ay * ay;
 }
 
+// One node of a periodic sweep shared by the lane pair (2j, 2j + 1) of a warp (pair form,
+// lbm_fixed.cuh): lane h pulls the populations k = h, h + 2, h + 4, h + 6 and the force
+// (adjoint source) component h, and writes its four outputs.  it2 counts half-nodes
+// (node it2 / 2); every lane of the warp must call it (inactive lanes, it2 >= nitems2,
+// work on node 0 and store nothing).  Nodes outside the fixed-point range take the FP64
+// pipe with the pair's ten inputs gathered by shuffles (all-zero nodes map to zero).
+template <int KIND, bool FIELD, bool MON>
+__device__ __forceinline__ void pair_item(const double *fin, double *fout,
+                                          const double *__restrict__ src2, const Grid &g,
+                                          const Coef &c0, const Field &fl, long it2,
+                                          long nitems2, double &mon) {
+  const int h = threadIdx.x & 1;
+  const bool act = it2 < nitems2;
+  const long n = act ? (it2 >> 1) : 0;
+  const int x = (int)(n % g.nx), y = (int)(n / g.nx);
+  double in[4], out[4], m = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = h + 2 * j;
+    const int dx = KIND == 0 ? -kCX[k] : kCX[k], dy = KIND == 0 ? -kCY[k] : kCY[k];
+    in[j] = fin[k * g.N + wrap_idx(x, y, dx, dy, g)];
+  }
+  const double q = __ldg(src2 + h * g.N + n);
+  const CoefFix cf = node_fix<FIELD>(c0.fx, fl, g.N, n);
+  const bool ok = KIND == 0 ? collide_fix_pair<MON, true>(in, q, h, cf, out, m)
+                            : collide_T_fix_pair<MON, true>(in, q, h, cf, out, m);
+  if (__any_sync(0xffffffffu, !ok)) {
+    double oth[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) oth[j] = __shfl_xor_sync(0xffffffffu, in[j], 1);
+    const double q_o = __shfl_xor_sync(0xffffffffu, q, 1);
+    if (!ok) {
+      double f[8], o[8], d1 = 0.0, d2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // (selects keep the arrays in registers)
+        f[2 * j] = h ? oth[j] : in[j];
+        f[2 * j + 1] = h ? in[j] : oth[j];
+      }
+      const double qx = h ? q_o : q, qy = h ? q : q_o;
+      if (!zero_node(f, qx, qy, o)) {
+        const Coef cc = node_coef<FIELD>(c0, fl, g.N, n, -1);
+        if (KIND == 0)
+          collide<false>(f, qx, qy, cc, o, d1, d2);
+        else
+          collide_T<false>(f, qx, qy, cc, o, d1, d2);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[j] = h ? o[2 * j + 1] : o[2 * j];
+      if (MON) m = h ? d2 : d1;
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fout[(h + 2 * j) * g.N + n] = out[j];
+    if (MON) mon += m * m;
+  }
+}
+
+// One sweep of the cluster's items (k_sweeps_cl): one node per thread, or (PAIR) one
+// node per lane pair over a warp-uniform loop.
+template <int KIND, bool BOUNDED, int ARITH, bool FIELD, bool MON, bool PAIR>
+__device__ __forceinline__ void cluster_sweep(const double *in, double *out,
+                                              const double *__restrict__ src2, const Grid &g,
+                                              const Bounded &b, const Compact &c,
+                                              const Coef &c0, const Field &fl,
+                                              const ClusterWork &w, long t0, long T,
+                                              double &mon) {
+  if (PAIR) {
+    const long n2 = 2 * w.nitems, lane = threadIdx.x & 31;
+    for (long b0 = t0 - lane; b0 < n2; b0 += T)
+      pair_item<KIND, FIELD, MON>(in, out, src2, g, c0, fl, b0 + lane, n2, mon);
+    return;
+  }
+  for (long i = t0; i < w.nitems; i += T) {
+    if (KIND == 0)
+      primal_item<BOUNDED, ARITH, FIELD, MON>(in, out, src2, g, b, c, c0, fl, w, i, mon);
+    else
+      adjoint_item<BOUNDED, ARITH, FIELD, MON>(in, out, src2, g, b, c, c0, fl, w, i, mon);
+  }
+}
+
 // `nsweeps` sweeps (KIND 0 primal, 1 adjoint) from buffer a (the state) to a or b
 // (b after an odd count).  With monitor, the last sweep's partial sums of |d|^2 go to
 // partial[rank] and partial[ncta .. npartial) are zeroed, so the usual finishing pass
@@ -1384,8 +1465,9 @@ __device__ __forceinline__ void adjoint_item(const double *pin, double *pout,
 // of `first` sweeps, then chunks of `chunk`, each followed by the residual of its last
 // two states and the cluster-wide decision (cluster_residual_stop), at most max_iters
 // chunks; ls receives the chunks run and the last residual (the state ends in b after
-// an odd total of sweeps, as for nsweeps).
-template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
+// an odd total of sweeps, as for nsweeps).  PAIR: one node per lane pair (periodic,
+// fixed point; the host launches twice the threads).
+template <int KIND, bool BOUNDED, int ARITH, bool FIELD, bool PAIR>
 __global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
                                                     const double *__restrict__ src2, Grid g,
                                                     Bounded b, Compact c, Coef c0, Field fl,
@@ -1406,12 +1488,8 @@ __global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
       for (int s = 0; s < len; ++s) {
         const double *in = par ? b2 : a;
         double *out = par ? a : b2;
-        for (long i = t0; i < w.nitems; i += T) {
-          if (KIND == 0)
-            primal_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, i, mon[0]);
-          else
-            adjoint_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, i, mon[0]);
-        }
+        cluster_sweep<KIND, BOUNDED, ARITH, FIELD, false, PAIR>(in, out, src2, g, b, c, c0, fl,
+                                                                 w, t0, T, mon[0]);
         cluster_sync_release_acquire();
         par ^= 1;
       }
@@ -1440,21 +1518,12 @@ __global__ void __launch_bounds__(256) k_sweeps_cl(double *a, double *b2,
   for (int s = 0; s < nsweeps; ++s) {
     const double *in = (s & 1) ? b2 : a;
     double *out = (s & 1) ? a : b2;
-    if (monitor && s == nsweeps - 1) {
-      for (long it = t0; it < w.nitems; it += T) {
-        if (KIND == 0)
-          primal_item<BOUNDED, ARITH, FIELD, true>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
-        else
-          adjoint_item<BOUNDED, ARITH, FIELD, true>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
-      }
-    } else {
-      for (long it = t0; it < w.nitems; it += T) {
-        if (KIND == 0)
-          primal_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
-        else
-          adjoint_item<BOUNDED, ARITH, FIELD, false>(in, out, src2, g, b, c, c0, fl, w, it, mon[0]);
-      }
-    }
+    if (monitor && s == nsweeps - 1)
+      cluster_sweep<KIND, BOUNDED, ARITH, FIELD, true, PAIR>(in, out, src2, g, b, c, c0, fl, w,
+                                                              t0, T, mon[0]);
+    else
+      cluster_sweep<KIND, BOUNDED, ARITH, FIELD, false, PAIR>(in, out, src2, g, b, c, c0, fl, w,
+                                                               t0, T, mon[0]);
     cluster_sync_release_acquire();
   }
   if (monitor) {

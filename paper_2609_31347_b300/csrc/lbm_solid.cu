@@ -58,6 +58,7 @@ struct lbm_solid {
   // cluster-resident sweeps of small periodic lattices (0 CTAs: not used)
   ClusterWork cw{};
   int cl_ncta = 0, cl_threads = 0;
+  bool cl_pair = false;  // one node per lane pair (k_sweeps_cl PAIR)
   // lattice resident in distributed shared memory (0 CTAs: not used)
   int dsm_ncta = 0, dsm_h = 0, dsm_threads = 0;
   size_t dsm_smem = 0;
@@ -282,11 +283,11 @@ constexpr long kClusterMaxItems = 2048;
 constexpr int kClusterMaxCta = 16;            // one GPC (non-portable cluster size)
 constexpr long kClusterChunk = 512;           // sweeps per launch (fixed-step runs)
 
-template <int KIND, bool BOUNDED, int ARITH, bool FIELD>
+template <int KIND, bool BOUNDED, int ARITH, bool FIELD, bool PAIR = false>
 cudaError_t launch_cluster(lbm_solid *h, int nsweeps, bool monitor, bool probe = false,
                            int *fits = nullptr, int chunk = 0, long long max_iters = 0,
                            double tol = 0.0, int first = 0) {
-  auto kern = k_sweeps_cl<KIND, BOUNDED, ARITH, FIELD>;
+  auto kern = k_sweeps_cl<KIND, BOUNDED, ARITH, FIELD, PAIR>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h->cl_ncta);
   cfg.blockDim = dim3((unsigned)h->cl_threads);
@@ -318,9 +319,13 @@ cudaError_t launch_cluster_any(lbm_solid *h, int nsweeps, bool monitor, bool pro
   const bool fp = h->kernel == LBM_KERNEL_FP64;
   if (h->field)
     return fp ? launch_cluster<KIND, false, 0, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first)
-              : launch_cluster<KIND, false, 1, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first);
+              : h->cl_pair
+                    ? launch_cluster<KIND, false, 1, true, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first)
+                    : launch_cluster<KIND, false, 1, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first);
   return fp ? launch_cluster<KIND, false, 0, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first)
-            : launch_cluster<KIND, false, 1, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first);
+            : h->cl_pair
+                  ? launch_cluster<KIND, false, 1, false, true>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first)
+                  : launch_cluster<KIND, false, 1, false>(h, nsweeps, monitor, probe, fits, chunk, max_iters, tol, first);
 }
 
 // Launch shape of the compact sweep of a bounded grid.  Below ~32 warps per SM the sweep
@@ -429,14 +434,17 @@ void setup_dsm(lbm_solid *h) {
 
 // Chooses the cluster shape for a small lattice (CTAs of whole warps, about one item per
 // thread, as many CTAs as a GPC allows) and checks that such a cluster can be scheduled;
-// otherwise the handle keeps the graph-replayed launches.
+// otherwise the handle keeps the graph-replayed launches.  With at most 64 nodes per CTA
+// (2 warps: half the SM sub-partitions idle) the fixed-point sweeps run in pair form, two
+// lanes per node.
 void setup_cluster(lbm_solid *h, long items) {
   h->cl_ncta = 0;
   if (items < 1 || items > kClusterMaxItems) return;
   for (int ncta = (int)std::min<long>(kClusterMaxCta, (items + 31) / 32); ncta >= 1; ncta /= 2) {
     const long per = (items + ncta - 1) / ncta;
     h->cl_ncta = ncta;
-    h->cl_threads = (int)std::min<long>(256, (per + 31) / 32 * 32);
+    h->cl_pair = h->periodic && h->kernel != LBM_KERNEL_FP64 && per <= 64;
+    h->cl_threads = (int)std::min<long>(256, ((h->cl_pair ? 2 : 1) * per + 31) / 32 * 32);
     int f0 = 0, f1 = 0;
     if (launch_cluster_any<0>(h, 0, false, true, &f0) == cudaSuccess && f0 > 0 &&
         launch_cluster_any<1>(h, 0, false, true, &f1) == cudaSuccess && f1 > 0) {
